@@ -1,0 +1,169 @@
+/*
+ * sem.h -- C ABI of libsem: matrix-free tensor-product GLL spectral-element
+ * operators for periodic viscous Burgers, their tangent and transpose products,
+ * and the explicit Runge-Kutta forward / discrete-adjoint sweeps built on them,
+ * on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Marin, Constantinescu, Smith, "A scalable matrix-free spectral element
+ * approach for unsteady PDE constrained optimization using PETSc/TAO",
+ * arXiv:1806.01422.  Each entry point names the section / equation it implements.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Grid.  d in {1,2,3}; E elements per direction; order N (n = N+1 GLL points per
+ *   direction); periodic box [0, L)^d, L = 2*pi for d = 1 and 1 otherwise unless
+ *   sem_opts.L is set.  Unique nodes per direction G = E*N.
+ * Vectors.  A "state" is d*G^d doubles (sem_ndof), structure of arrays by
+ *   component: index ((c*G + g_{d-1})*G + ...)*G + g_0, so x_0 is the fastest
+ *   index.  Component c is the velocity along x_c (d = 1: the scalar u).
+ *   Node g along an axis sits at x = e*h + (xi_i + 1)*h/2 with e = g / N,
+ *   i = g % N, h = L/E and xi the GLL points on [-1, 1] (sem_coords).
+ * Pointers.  State pointers are DEVICE pointers owned by the caller, 8-byte
+ *   aligned, not overlapping any output of the same call (else SEM_ERR_ALIAS).
+ *   `stream` is a cudaStream_t (NULL = legacy default stream).  Every call is
+ *   stream-ordered and returns after enqueueing, except where a host output
+ *   (J_host) is documented as synchronising the stream.
+ * Ownership.  The handle owns its workspaces, the forward trajectory and the
+ *   checkpoint slots; they are allocated on first use on the device current at
+ *   that time and freed by sem_destroy.
+ * Errors.  Every int-returning call returns SEM_OK (0) or a negative code;
+ *   sem_last_error() returns a thread-local message for the last failure.
+ *   Argument errors are detected on the host before anything is enqueued.
+ */
+#ifndef SEM_H
+#define SEM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sem_ctx* sem_t;
+
+/* status codes */
+#define SEM_OK             0
+#define SEM_ERR_ARG       -1  /* bad dimension, size, order, pointer or option */
+#define SEM_ERR_ALIAS     -2  /* an output overlaps an input */
+#define SEM_ERR_OOM       -3  /* device allocation failed or checkpoint budget exceeded */
+#define SEM_ERR_NONFINITE -4  /* a NaN/Inf appeared in the forward or adjoint sweep */
+#define SEM_ERR_STATE     -5  /* sem_rk_adjoint without a completed sem_rk_forward */
+#define SEM_ERR_CUDA      -6  /* a CUDA runtime call failed (message has the CUDA error) */
+
+/* explicit Runge-Kutta schemes (Butcher tableaux) */
+#define SEM_RK4      0  /* classic 4-stage, 4th order */
+#define SEM_SSPRK3   1  /* Shu-Osher SSP 3-stage, 3rd order */
+#define SEM_EULER    2  /* forward Euler (the case of Sec. 4.1) */
+
+/* arithmetic of the element kernels */
+#define SEM_PREC_FP64       0  /* everything in FP64 */
+#define SEM_PREC_FP32_BULK  1  /* FP32 contractions and pointwise products; FP64
+                                  gather-scatter sums, RK stage accumulation,
+                                  objective and adjoint accumulation */
+
+/* trajectory storage for the adjoint sweep (Sec. 5.3, Sec. 5.4) */
+#define SEM_CKPT_AUTO      0  /* STAGES if it fits ckpt_budget_bytes, else STATES, else BINOMIAL */
+#define SEM_CKPT_STAGES    1  /* store every stage value of every step: adjoint = s J^T per step */
+#define SEM_CKPT_STATES    2  /* store every step's state; recompute its stages in the adjoint */
+#define SEM_CKPT_BINOMIAL  3  /* ckpt_slots state slots, revolve-optimal recomputation */
+
+typedef struct {
+    int    dim;                /* 1, 2 or 3 */
+    int    E;                  /* elements per direction, >= 1 (>= 2 recommended) */
+    int    N;                  /* polynomial order, 1..15 (n = N+1 <= 16 points) */
+    double nu;                 /* viscosity, >= 0 */
+    double L;                  /* box edge; <= 0 selects the default (2 pi for d = 1, else 1) */
+    int    precision;          /* SEM_PREC_* */
+    int    ckpt_mode;          /* SEM_CKPT_* */
+    int    ckpt_slots;         /* BINOMIAL: number of state slots (>= 1) */
+    size_t ckpt_budget_bytes;  /* device bytes the trajectory may use; 0 = no limit */
+} sem_opts;
+
+/* Create a handle for the periodic grid of Sec. 3.2 (affine elements, GLL basis).
+ * Host-only: computes the GLL tables; no device memory is touched.
+ * Returns SEM_ERR_ARG for dim not in {1,2,3}, E < 1, N not in [1,15], nu < 0,
+ * non-finite nu, or a null `out`. */
+int sem_create(int dim, int E, int N, double nu, sem_t* out);
+int sem_create_ex(const sem_opts* opts, sem_t* out);
+
+/* Free the handle and every device buffer it owns (after synchronising the device
+ * work the handle enqueued).  NULL is ignored. */
+void sem_destroy(sem_t h);
+
+/* d * (E*N)^d: unique periodic scalar unknowns (Sec. 6.3 counts unknowns this way). */
+size_t sem_ndof(sem_t h);
+
+/* Host array x[G]: coordinates of the unique nodes along one axis (same on every axis). */
+int sem_coords(sem_t h, double* x_host);
+
+/* f = F(u) = M^-1 Q^T [ -nu sum_j D_j^T B D_j Q u_c - B sum_j (Q u_j) o D_j (Q u_c) ]
+ * Eq. rhsvec (Sec. 3.3) with the sign of Eq. burgers23d, in the explicit form
+ * du/dt = M^-1 P[u] of Sec. 3.4.  u, f: device states. */
+int sem_rhs(sem_t h, const double* u, double* f, void* stream);
+
+/* jw = J(u) w, the tangent of sem_rhs (eq. jacvec). */
+int sem_jac_apply(sem_t h, const double* u, const double* w, double* jw, void* stream);
+
+/* jtv = J(u)^T v, the Euclidean transpose of sem_jac_apply (eq. jactransvec, the
+ * paper's contribution): jtv = Q^T L^T Q M^-1 v with one shared divergence for the
+ * viscous and D_j^T[u_j o w] terms. */
+int sem_jacT_apply(sem_t h, const double* u, const double* v, double* jtv, void* stream);
+
+/* Forward sweep (Sec. 4.1, Fig. 1): u_{k+1} = RK step of u_k for k < nsteps, from
+ * u0 to uT (device states; uT must not overlap u0).  Stores what the adjoint
+ * needs according to the
+ * handle's checkpoint mode.  dt > 0, nsteps >= 1.  Returns SEM_ERR_NONFINITE if
+ * the final state is not finite (the check synchronises the stream), SEM_ERR_OOM
+ * if the trajectory does not fit the budget or the device. */
+int sem_rk_forward(sem_t h, int scheme, double dt, int nsteps,
+                   const double* u0, double* uT, void* stream);
+
+/* Backward sweep: lam0 = (d u_N / d u_0)^T lamT along the last forward sweep
+ * (eqs. adjointloop, initadj, gradient with the RK tableau; Euclidean adjoint).
+ * SEM_ERR_STATE if no forward sweep was recorded.  Checks finiteness like
+ * sem_rk_forward. */
+int sem_rk_adjoint(sem_t h, const double* lamT, double* lam0, void* stream);
+
+/* J_host = 1/2 (u - u_obs)^T M (u - u_obs) and lam = M (u - u_obs) (eqs. ourcost,
+ * initadj).  Synchronises `stream` to write *J_host.  lam may be NULL. */
+int sem_objective(sem_t h, const double* u, const double* u_obs,
+                  double* J_host, double* lam, void* stream);
+
+/* One gradient evaluation of the misfit J(u0) = 1/2 ||u_N(u0) - u_obs||_M^2
+ * (Fig. 1): forward sweep, objective, terminal adjoint, backward sweep.
+ * grad = dJ/du0 (Euclidean).  Synchronises `stream` to write *J_host. */
+int sem_objective_grad(sem_t h, int scheme, double dt, int nsteps,
+                       const double* u0, const double* u_obs,
+                       double* J_host, double* grad, void* stream);
+
+/* Host-only: optimal number of extra forward steps (advances) the binomial
+ * schedule spends to reverse `nsteps` steps from a stored start state with
+ * `slots` further state slots (Sec. 5.3, revolve).  Returns SEM_ERR_ARG for
+ * nsteps < 1, slots < 0 or a null pointer. */
+int sem_ckpt_plan(int nsteps, int slots, long long* advances);
+
+/* Work counters of the last sweeps on this handle: out3[0] = F applies in the
+ * last forward sweep, out3[1] = F applies the last adjoint sweep spent on
+ * recomputation (stage taping and checkpoint replays), out3[2] = J^T applies in
+ * the last adjoint sweep.  Host-only. */
+int sem_sweep_stats(sem_t h, long long* out3);
+
+/* Opt-in kernel timing (no counterpart in the paper; used by the benchmarks).
+ * While enabled, every kernel launch of an operator apply on this handle is
+ * bracketed by a pair of CUDA events on its stream.  sem_profile_read waits for
+ * the recorded events and returns the summed device time in ms (ms4) and the
+ * launch count (count4) per kind: [0] F element kernel, [1] J element kernel,
+ * [2] J^T element kernel, [3] gather-scatter assembly; reset != 0 clears them.
+ * Enabling costs two event records per launch and a stream wait every 4096
+ * launches. */
+int sem_profile(sem_t h, int enable);
+int sem_profile_read(sem_t h, double* ms4, long long* count4, int reset);
+
+/* Thread-local text of the last error ("" if none). */
+const char* sem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEM_H */

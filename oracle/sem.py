@@ -16,7 +16,7 @@ Notation used below (every symbol is a plain array):
   ``(d, G, .., G)`` with the LAST axis the x_0 (fastest) direction; component c
   is the velocity along physical direction x_c, i.e. array axis d-1-c.
 * ``Q``: periodic scatter global -> element-local ("gather"), shape
-  ``(d, E, .., E, n, .., n)``; ``Q^T``: sum of element contributions.
+  ``(d, E^d, n, .., n)``; ``Q^T``: sum of element contributions.
 * ``B``: element-local diagonal GLL mass (h/2)^d w (x) w (x) w.
 * ``M = Q^T B 1``: global diagonal mass.
 * ``D_j``: collocation derivative along direction j, (2/h) Dhat.
@@ -49,26 +49,24 @@ class Grid:
         e = np.arange(E)[:, None]
         i = np.arange(self.n)[None, :]
         self._idx1 = (e * N + i) % self.G
+        self.nelem = E ** dim
+        # B: element-local GLL mass (Sec. 3.2, M_1 = (L/2) M per direction with L = h),
+        # shape (1, n, .., n) to broadcast over a flat element axis
         d = dim
-        self._idx = []
+        Bn = np.ones([1] + [self.n] * d)
         for p in range(d):
-            # open-mesh index array for array axis p: element axis p, node axis d + p
-            shape = [1] * (2 * d)
-            shape[p] = E
-            shape[d + p] = self.n
-            self._idx.append(self._idx1.reshape(shape))
-        # B: element-local GLL mass (Sec. 3.2, M_1 = (L/2) M per direction with L = h)
-        Bn = np.ones([1] * d + [self.n] * d)
-        for p in range(d):
-            shape = [1] * (2 * d)
-            shape[d + p] = self.n
+            shape = [1] * (1 + d)
+            shape[1 + p] = self.n
             Bn = Bn * self.w.reshape(shape)
         self.B = (self.h / 2.0) ** d * Bn
         self.M = self.scatter_add(np.broadcast_to(self.B, self.local_shape()))
 
     # ----------------------------------------------------------------- layout
-    def local_shape(self):
-        return (self.E,) * self.d + (self.n,) * self.d
+    # Elements are numbered e = ((e_{d-1} E) + ..) E + e_0 (e_0 along x_0, fastest);
+    # element-local arrays have shape (nelem, n, .., n) with the node axes in
+    # array order (x_{d-1}, .., x_0).
+    def local_shape(self, nsel=None):
+        return (self.nelem if nsel is None else nsel,) + (self.n,) * self.d
 
     def global_shape(self):
         return (self.G,) * self.d
@@ -82,19 +80,38 @@ class Grid:
         e, i = g // self.N, g % self.N
         return e * self.h + (self.xi[i] + 1.0) * self.h / 2.0
 
-    def gather(self, u):
-        """Q: global scalar field (G,..,G) -> element-local (E,..,E, n,..,n)."""
-        return u[tuple(self._idx)]
+    def elem_coords(self, elems):
+        """Per-direction element coordinates (array order: e_{d-1}, .., e_0) of element ids."""
+        elems = np.asarray(elems)
+        out = []
+        for p in range(self.d):
+            out.append((elems // self.E ** (self.d - 1 - p)) % self.E)
+        return out
+
+    def _open_index(self, elems):
+        ec = self.elem_coords(elems)
+        idx = []
+        for p in range(self.d):
+            shape = [1] * (1 + self.d)
+            shape[0] = len(ec[p])
+            shape[1 + p] = self.n
+            idx.append(self._idx1[ec[p]].reshape(shape))
+        return tuple(idx)
+
+    def gather(self, u, elems=None):
+        """Q: global scalar field (G,..,G) -> element-local (nsel, n,..,n) (all elements by default)."""
+        elems = np.arange(self.nelem) if elems is None else elems
+        return u[self._open_index(elems)]
 
     def scatter_add(self, U):
-        """Q^T: element-local -> global, summing the copies of shared nodes."""
+        """Q^T: element-local (nelem, n,..,n) -> global, summing the copies of shared nodes."""
         out = np.zeros(self.global_shape())
-        np.add.at(out, tuple(self._idx), U)
+        np.add.at(out, self._open_index(np.arange(self.nelem)), U)
         return out
 
     def node_axis(self, j):
         """Array axis of the element-local tile along physical direction x_j."""
-        return self.d + (self.d - 1 - j)
+        return 1 + (self.d - 1 - j)
 
     def apply_1d(self, A, X, axis):
         """Y[.., a, ..] = sum_m A[a, m] X[.., m, ..] along one axis (one Kronecker factor)."""
@@ -108,34 +125,29 @@ class Grid:
         """D_j^T X = (2/h) Dhat^T along direction x_j."""
         return (2.0 / self.h) * self.apply_1d(self.Dh.T, X, self.node_axis(j))
 
-    def gather_vec(self, u):
-        return np.stack([self.gather(u[c]) for c in range(self.d)])
+    def gather_vec(self, u, elems=None):
+        return np.stack([self.gather(u[c], elems) for c in range(self.d)])
 
     def scatter_vec(self, R):
         return np.stack([self.scatter_add(R[c]) for c in range(self.d)])
 
     # -------------------------------------------------------------- operators
-    def rhs(self, u):
-        """F(u) = M^-1 Q^T [ -nu sum_j D_j^T B D_j U_c - B sum_j U_j o D_j U_c ]  (eq. rhsvec).
-
-        Eq. discrete3d gives M du/dt = nu K u - u . G u with K = sum_j D_j^T B D_j
-        entering with the sign fixed by Eq. burgers23d (negative semidefinite
-        viscous operator, minus the advection).
-        """
+    # Element-local residuals r_e (B-weighted, before the sum Q^T); each takes
+    # element-local arrays of any number of elements.
+    def local_rhs(self, U):
+        """-nu sum_j D_j^T B D_j U_c - B sum_j U_j o D_j U_c  (eq. rhsvec, sign of Eq. burgers23d)."""
         d, B = self.d, self.B
-        U = self.gather_vec(u)
         R = np.empty_like(U)
         for c in range(d):
             g = [self.grad(U[c], j) for j in range(d)]
             visc = sum(self.gradT(B * g[j], j) for j in range(d))
             adv = sum(U[j] * g[j] for j in range(d))
             R[c] = -self.nu * visc - B * adv
-        return self.scatter_vec(R) / self.M
+        return R
 
-    def jac(self, u, w):
-        """J(u) w = M^-1 Q^T [ -nu sum_j D_j^T B D_j W_c - B sum_j (W_j o D_j U_c + U_j o D_j W_c) ]  (eq. jacvec)."""
+    def local_jac(self, U, W):
+        """-nu sum_j D_j^T B D_j W_c - B sum_j (W_j o D_j U_c + U_j o D_j W_c)  (eq. jacvec)."""
         d, B = self.d, self.B
-        U, W = self.gather_vec(u), self.gather_vec(w)
         R = np.empty_like(U)
         for c in range(d):
             gU = [self.grad(U[c], j) for j in range(d)]
@@ -143,7 +155,31 @@ class Grid:
             visc = sum(self.gradT(B * gW[j], j) for j in range(d))
             adv = sum(W[j] * gU[j] + U[j] * gW[j] for j in range(d))
             R[c] = -self.nu * visc - B * adv
-        return self.scatter_vec(R) / self.M
+        return R
+
+    def local_jacT(self, U, Z):
+        """(L^T z)_l = -sum_j D_j^T( B o (nu D_j z_l + U_j o z_l) ) - B o sum_c z_c o D_l U_c  (eq. jactransvec)."""
+        d, B = self.d, self.B
+        R = np.empty_like(U)
+        for l in range(d):
+            flux = sum(self.gradT(B * (self.nu * self.grad(Z[l], j) + U[j] * Z[l]), j)
+                       for j in range(d))
+            react = sum(Z[c] * self.grad(U[c], l) for c in range(d))
+            R[l] = -flux - B * react
+        return R
+
+    def rhs(self, u):
+        """F(u) = M^-1 Q^T [ -nu sum_j D_j^T B D_j U_c - B sum_j U_j o D_j U_c ]  (eq. rhsvec).
+
+        Eq. discrete3d gives M du/dt = nu K u - u . G u with K = sum_j D_j^T B D_j
+        entering with the sign fixed by Eq. burgers23d (negative semidefinite
+        viscous operator, minus the advection).
+        """
+        return self.scatter_vec(self.local_rhs(self.gather_vec(u))) / self.M
+
+    def jac(self, u, w):
+        """J(u) w = M^-1 Q^T [ -nu sum_j D_j^T B D_j W_c - B sum_j (W_j o D_j U_c + U_j o D_j W_c) ]  (eq. jacvec)."""
+        return self.scatter_vec(self.local_jac(self.gather_vec(u), self.gather_vec(w))) / self.M
 
     def jacT(self, u, v):
         """J(u)^T v, the Euclidean transpose of ``jac`` (eq. jactransvec).
@@ -154,16 +190,50 @@ class Grid:
         The three terms are eq. jactransvec's K_j^T[w_i], D_j^T[u_j o w_i] and
         w_j o D_i[u_j]; the 1D print u o D^T[w] is read as D^T[u o w].
         """
-        d, B = self.d, self.B
-        U = self.gather_vec(u)
-        Z = self.gather_vec(v / self.M)
-        R = np.empty_like(U)
-        for l in range(d):
-            flux = sum(self.gradT(B * (self.nu * self.grad(Z[l], j) + U[j] * Z[l]), j)
-                       for j in range(d))
-            react = sum(Z[c] * self.grad(U[c], l) for c in range(d))
-            R[l] = -flux - B * react
-        return self.scatter_vec(R)
+        return self.scatter_vec(self.local_jacT(self.gather_vec(u), self.gather_vec(v / self.M)))
+
+    # ------------------------------------------- single-node evaluation (sampling)
+    def sharing(self, node):
+        """Elements sharing a global node (array-order index tuple) and its local index in each."""
+        choices = []
+        for p in range(self.d):
+            g = node[p]
+            e, i = g // self.N, g % self.N
+            opts = [(e, i)]
+            if i == 0:
+                opts.append(((e - 1) % self.E, self.N))
+            choices.append(opts)
+        out = []
+        for combo in np.ndindex(*[len(c) for c in choices]):
+            ec = [choices[p][combo[p]] for p in range(self.d)]
+            eid = 0
+            for p in range(self.d):
+                eid = eid * self.E + ec[p][0]
+            out.append((eid, tuple(ec[p][1] for p in range(self.d))))
+        return out
+
+    def _at(self, local_fn, fields, nodes, divide_by_mass):
+        vals = np.empty((self.d, len(nodes)))
+        for k, node in enumerate(nodes):
+            sh = self.sharing(node)
+            elems = [e for e, _ in sh]
+            R = local_fn(*[self.gather_vec(f, elems) for f in fields])
+            for c in range(self.d):
+                v = sum(R[(c, s) + loc] for s, (_, loc) in enumerate(sh))
+                vals[c, k] = v / self.M[node] if divide_by_mass else v
+        return vals
+
+    def rhs_at(self, u, nodes):
+        """F(u) at the listed global nodes only, from the elements sharing each node: shape (d, len(nodes))."""
+        return self._at(self.local_rhs, [u], nodes, True)
+
+    def jacT_at(self, u, v, nodes):
+        """(J(u)^T v) at the listed global nodes only."""
+        return self._at(self.local_jacT, [u, v / self.M], nodes, False)
+
+    def jac_at(self, u, w, nodes):
+        """(J(u) w) at the listed global nodes only."""
+        return self._at(self.local_jac, [u, w], nodes, True)
 
     # -------------------------------------------------------------- objective
     def objective(self, u, u_obs):

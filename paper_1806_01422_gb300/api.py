@@ -1,0 +1,170 @@
+"""Python front end of libsem over torch tensors (device memory and streams only).
+
+Every operation is one call into the C ABI; torch supplies the CUDA buffers and
+the current stream.  Inputs may be CPU tensors or numpy arrays for the
+end-to-end form: they are copied to the device (pinned host memory when given)
+and results copied back, which is the host-buffer path the benchmarks time.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+SCHEMES = {"rk4": L.SEM_RK4, "ssprk3": L.SEM_SSPRK3, "euler": L.SEM_EULER}
+PRECISIONS = {"fp64": L.SEM_PREC_FP64, "fp32_bulk": L.SEM_PREC_FP32_BULK}
+CKPT = {"auto": L.SEM_CKPT_AUTO, "stages": L.SEM_CKPT_STAGES, "states": L.SEM_CKPT_STATES,
+        "binomial": L.SEM_CKPT_BINOMIAL}
+
+
+def _stream(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class Sem:
+    """Periodic d-dimensional viscous Burgers on E^d GLL elements of order N (one GPU)."""
+
+    def __init__(self, dim, E, N, nu, L_box=None, precision="fp64", ckpt="auto", ckpt_slots=0,
+                 ckpt_budget_bytes=0, device=None):
+        o = L.sem_opts(dim=dim, E=E, N=N, nu=float(nu), L=float(L_box or 0.0),
+                       precision=PRECISIONS[precision], ckpt_mode=CKPT[ckpt], ckpt_slots=ckpt_slots,
+                       ckpt_budget_bytes=ckpt_budget_bytes)
+        h = ctypes.c_void_p()
+        L.check(L.lib().sem_create_ex(ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self.dim, self.E, self.N, self.nu = dim, E, N, float(nu)
+        self.G = E * N
+        self.ndof = int(L.lib().sem_ndof(h))
+        self.shape = (dim,) + (self.G,) * dim
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device()) \
+            if torch.cuda.is_available() else torch.device("cpu")
+
+    # ------------------------------------------------------------ lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            L.lib().sem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ helpers
+    def coords(self):
+        x = np.empty(self.G)
+        L.check(L.lib().sem_coords(self._h, x.ctypes.data_as(ctypes.c_void_p)))
+        return x
+
+    def empty(self):
+        return torch.empty(self.shape, dtype=torch.float64, device=self.device)
+
+    def _dev(self, t, name):
+        if isinstance(t, np.ndarray):
+            t = torch.from_numpy(np.ascontiguousarray(t, dtype=np.float64))
+        if not isinstance(t, torch.Tensor):
+            raise TypeError("%s must be a tensor or ndarray" % name)
+        if t.dtype != torch.float64:
+            raise TypeError("%s must be float64" % name)
+        if t.numel() != self.ndof:
+            raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), self.ndof))
+        if t.device.type != "cuda":
+            t = t.to(self.device, non_blocking=t.is_pinned())
+        return t.contiguous().view(self.shape)
+
+    @staticmethod
+    def _p(t):
+        return ctypes.c_void_p(t.data_ptr())
+
+    # ------------------------------------------------------------ operators
+    def rhs(self, u, out=None):
+        u = self._dev(u, "u")
+        out = self.empty() if out is None else out
+        L.check(L.lib().sem_rhs(self._h, self._p(u), self._p(out), _stream(self.device)))
+        return out
+
+    def jac(self, u, w, out=None):
+        u, w = self._dev(u, "u"), self._dev(w, "w")
+        out = self.empty() if out is None else out
+        L.check(L.lib().sem_jac_apply(self._h, self._p(u), self._p(w), self._p(out), _stream(self.device)))
+        return out
+
+    def jacT(self, u, v, out=None):
+        u, v = self._dev(u, "u"), self._dev(v, "v")
+        out = self.empty() if out is None else out
+        L.check(L.lib().sem_jacT_apply(self._h, self._p(u), self._p(v), self._p(out), _stream(self.device)))
+        return out
+
+    # ------------------------------------------------------------ sweeps
+    def rk_forward(self, u0, dt, nsteps, scheme="rk4", out=None):
+        u0 = self._dev(u0, "u0")
+        out = self.empty() if out is None else out
+        L.check(L.lib().sem_rk_forward(self._h, SCHEMES[scheme], float(dt), int(nsteps), self._p(u0),
+                                       self._p(out), _stream(self.device)))
+        return out
+
+    def rk_adjoint(self, lamT, out=None):
+        lamT = self._dev(lamT, "lamT")
+        out = self.empty() if out is None else out
+        L.check(L.lib().sem_rk_adjoint(self._h, self._p(lamT), self._p(out), _stream(self.device)))
+        return out
+
+    def objective(self, u, u_obs, lam=None):
+        u, u_obs = self._dev(u, "u"), self._dev(u_obs, "u_obs")
+        J = ctypes.c_double()
+        L.check(L.lib().sem_objective(self._h, self._p(u), self._p(u_obs), ctypes.byref(J),
+                                      self._p(lam) if lam is not None else None, _stream(self.device)))
+        return J.value
+
+    def objective_grad(self, u0, u_obs, dt, nsteps, scheme="rk4", grad=None, host=False):
+        """(J, dJ/du0).  With host=True the gradient is returned as a CPU tensor."""
+        u0, u_obs = self._dev(u0, "u0"), self._dev(u_obs, "u_obs")
+        grad = self.empty() if grad is None else grad
+        J = ctypes.c_double()
+        L.check(L.lib().sem_objective_grad(self._h, SCHEMES[scheme], float(dt), int(nsteps), self._p(u0),
+                                           self._p(u_obs), ctypes.byref(J), self._p(grad),
+                                           _stream(self.device)))
+        return J.value, (grad.cpu() if host else grad)
+
+    def profile(self, enable=True):
+        L.check(L.lib().sem_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self, reset=True):
+        """{kind: (ms, launches)} for kinds rhs, jac, jacT element kernels and assembly."""
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_longlong * 4)()
+        L.check(L.lib().sem_profile_read(self._h, ms, n, 1 if reset else 0))
+        return {k: (ms[i], n[i]) for i, k in enumerate(("rhs", "jac", "jacT", "assemble"))}
+
+    def sweep_stats(self):
+        out = (ctypes.c_longlong * 3)()
+        L.check(L.lib().sem_sweep_stats(self._h, out))
+        return {"forward_rhs": out[0], "adjoint_rhs": out[1], "adjoint_jacT": out[2]}
+
+
+def ckpt_plan(nsteps, slots):
+    """Optimal advance count of the binomial schedule (host only)."""
+    a = ctypes.c_longlong()
+    L.check(L.lib().sem_ckpt_plan(int(nsteps), int(slots), ctypes.byref(a)))
+    return a.value
+
+
+class SemMisfit(torch.autograd.Function):
+    """u0 -> J(u0) = 1/2 ||u_N(u0) - u_obs||_M^2 with backward = the discrete adjoint sweep.
+
+    forward runs sem_objective_grad once (forward sweep, misfit, adjoint sweep) and
+    keeps the gradient; backward scales it by the incoming gradient.
+    """
+
+    @staticmethod
+    def forward(ctx, u0, sem, u_obs, dt, nsteps, scheme):
+        J, g = sem.objective_grad(u0.detach(), u_obs, dt, nsteps, scheme)
+        ctx.save_for_backward(g)
+        return torch.tensor(J, dtype=torch.float64, device=u0.device)
+
+    @staticmethod
+    def backward(ctx, gJ):
+        (g,) = ctx.saved_tensors
+        return gJ * g, None, None, None, None, None

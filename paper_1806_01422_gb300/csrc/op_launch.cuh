@@ -1,0 +1,74 @@
+// Launch configuration of the element kernels: split the host matrices into
+// even/odd halves, size the block (elements per block x threads per element)
+// and the dynamic shared memory, and dispatch on the runtime point count.
+#pragma once
+#include <algorithm>
+
+#include "op_elem.cuh"
+#include "sem_internal.h"
+
+namespace semk {
+
+template <typename T, int NP>
+void split_eo(EOMat<T, NP>& M, const double* A) {
+    constexpr int H = NP / 2;
+    for (int i = 0; i < H; ++i) {
+        for (int j = 0; j < H; ++j) {
+            M.e[i][j] = (T)(0.5 * (A[i * NP + j] + A[i * NP + (NP - 1 - j)]));
+            M.o[i][j] = (T)(0.5 * (A[i * NP + j] - A[i * NP + (NP - 1 - j)]));
+        }
+        if (NP & 1) M.e[i][H] = (T)A[i * NP + H];
+        M.m[i] = (NP & 1) ? (T)A[H * NP + i] : (T)0;
+    }
+}
+
+constexpr int SMEM_TARGET = 100 * 1024;   // two blocks per SM fit in 227 KB
+
+template <typename T, int D, int NP>
+size_t elem_smem_bytes(int op) {
+    using Tl = Tile<NP>;
+    const size_t tile = D == 3 ? Tl::S3 : (D == 2 ? Tl::S2 : 0);
+    return (size_t)tiles_per_elem<D>(op) * tile * sizeof(T);
+}
+
+template <typename T, int D, int NP>
+cudaError_t launch_elem_np(int op, const double* mats, const ElemArgs& a, cudaStream_t s) {
+    OpMats<T, NP> M;
+    split_eo<T, NP>(M.Dg, mats + 0 * NP * NP);
+    split_eo<T, NP>(M.Dv, mats + 1 * NP * NP);
+    split_eo<T, NP>(M.Vz, mats + 2 * NP * NP);
+    split_eo<T, NP>(M.Dd, mats + 3 * NP * NP);
+    if (a.nelem <= 0) return cudaSuccess;
+    if constexpr (D == 1) {
+        const int threads = 128;
+        const int blocks = (a.nelem + threads - 1) / threads;
+        op1_kernel<T, NP><<<blocks, threads, 0, s>>>(M, a, op);
+        return cudaGetLastError();
+    } else {
+        constexpr int TPE = D == 3 ? NP * NP : NP;
+        const size_t per = elem_smem_bytes<T, D, NP>(op);
+        int epb = std::max(1, std::min(256 / TPE, (int)(SMEM_TARGET / per)));
+        epb = std::min(epb, a.nelem);
+        const size_t smem = per * epb;
+        if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+        const int threads = epb * TPE;
+        const int blocks = (a.nelem + epb - 1) / epb;
+        void (*k)(const OpMats<T, NP>, const ElemArgs);
+        if constexpr (D == 3)
+            k = op == OP_RHS ? rhs3_kernel<T, NP> : (op == OP_JAC ? jac3_kernel<T, NP> : jact3_kernel<T, NP>);
+        else
+            k = op == OP_RHS ? rhs2_kernel<T, NP> : (op == OP_JAC ? jac2_kernel<T, NP> : jact2_kernel<T, NP>);
+        if (smem > 48 * 1024) {
+            cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (err != cudaSuccess) return err;
+        }
+        k<<<blocks, threads, smem, s>>>(M, a);
+        return cudaGetLastError();
+    }
+}
+
+}  // namespace semk
+
+// Explicit dispatch over the point counts LO..HI of one (T, D) pair.
+#define SEMK_DISPATCH_CASE(T, D, NP) \
+    case NP: return launch_elem_np<T, D, NP>(op, mats, a, s);

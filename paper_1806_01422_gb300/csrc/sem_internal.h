@@ -1,0 +1,59 @@
+// Internal interfaces between the C-ABI host code and the CUDA kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "op_kernels.cuh"
+
+namespace semk {
+
+// Element kernel launch for dimension D, compute type T, runtime point count
+// np = N+1.  `mats` holds the four full np x np matrices Dg, Dv, Vz, Dd
+// (row-major, in that order); the launcher splits them into even/odd halves.
+template <typename T, int D>
+cudaError_t launch_elem(int np, int op, const double* mats, const ElemArgs& a, cudaStream_t s);
+
+// Largest supported point count per (D, T): limited by the shared-memory tiles.
+int max_np(int D, bool fp32);
+
+// --------------------------------------------------------------- assembly
+// Epilogue of the gather-scatter sum: for each unique scalar node with
+// assembled value a,  out[o] = alpha[o] a + sum_m beta[o][m] src[m]  (o < nout).
+struct Epi {
+    double* out[3];
+    double alpha[3];
+    const double* src[4];
+    double beta[3][4];
+    int nout, nsrc;
+    unsigned* nonfinite;  // set to 1 if any output is NaN/Inf (may be null)
+};
+
+struct AsmArgs {
+    int D, E, N, G, NP;
+    unsigned GD;       // G^D
+    unsigned ndof;     // D * G^D
+    int scale_mult;    // 1: multiply the sum by 1/k (F and J); 0: plain sum (J^T)
+};
+
+cudaError_t launch_assemble(bool lvec_fp32, const void* lvec, const AsmArgs& a, const Epi& ep,
+                            cudaStream_t s);
+
+// --------------------------------------------------------------- objective
+struct ObjArgs {
+    int D, N, G;
+    unsigned GD, ndof;
+    double mw[16];     // 1D assembled GLL weights by position i = g % N (i = 0 counts both neighbours)
+    double scale;      // (h/2)^D
+};
+// partials[nblocks] <- per-block sums of (u-uo) M (u-uo); lam <- M (u-uo) if lam != null
+cudaError_t launch_objective(const double* u, const double* uo, double* lam, double* partials,
+                             int nblocks, const ObjArgs& a, cudaStream_t s);
+// out[0] <- factor * sum(partials[0..n)) in a fixed order
+cudaError_t launch_sum_partials(const double* partials, int n, double* out, double factor,
+                                cudaStream_t s);
+int objective_blocks(unsigned ndof);
+
+// out <- alpha * in  (n doubles)
+cudaError_t launch_scale(double* out, const double* in, double alpha, size_t n, cudaStream_t s);
+
+}  // namespace semk
