@@ -1,0 +1,424 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the spectral-element Burgers gradient on GB300.
+
+One step = one gradient evaluation of the misfit J(u0) = 1/2 ||u_N(u0) - u_obs||_M^2
+for the 2D vector viscous Burgers workload (periodic [0,1]^2, 64x64 elements of
+order 7, 401,408 unknowns, nu = 1e-3, SSP-RK3, dt = 2e-4, 2000 steps, every
+stage value stored): forward sweep, misfit and terminal adjoint, backward sweep
+with the matrix-free transpose Jacobian, all on one GPU through the C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs one independent replica per GPU (torchrun, one rank per GPU): the
+path has no exchange step on one box, so scaling is weak.  Prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GDOF/s for F(u) and J^T v; adjoint/forward cost ratio; gradient evals/s"
+
+WORKLOADS = {
+    "2d": dict(dim=2, E=64, N=7, nu=1e-3, scheme="ssprk3", dt=2e-4, nsteps=2000, ckpt="stages", slots=0,
+               desc="2D vector viscous Burgers, periodic [0,1]^2, 64x64 quads, N=7 (401,408 unknowns), "
+                    "nu=1e-3, SSP-RK3 dt=2e-4 x 2000 steps, all stages stored; one gradient evaluation per step",
+               data="synthetic: seeded 16-mode Fourier fields (|k|_inf <= 8, amplitude ~|k|^-2, max|u0| = 1) "
+                    "for u0 (seed 1) and u_obs (seed 2)"),
+    "3d": dict(dim=3, E=32, N=7, nu=5e-4, scheme="rk4", dt=2.5e-4, nsteps=1000, ckpt="binomial", slots=20,
+               desc="3D vector viscous Burgers, periodic [0,1]^3, 32^3 hexes, N=7 (33,718,272 unknowns), "
+                    "nu=5e-4, RK4 dt=2.5e-4 x 1000 steps, binomial checkpointing with 20 slots",
+               data="synthetic: seeded random-phase fields, spectrum ~k^-5/3 cut at |k| = 16, max|u0| = 1"),
+    "1d": dict(dim=1, E=16, N=7, nu=0.01, scheme="rk4", dt=1e-3, nsteps=500, ckpt="stages", slots=0,
+               desc="1D viscous Burgers, periodic [0,2pi), 16 elements, N=7 (112 unknowns), nu=0.01, "
+                    "RK4 dt=1e-3 x 500 steps",
+               data="synthetic: u0 = sin x + 0.1 sum_k a_k sin(kx + phi_k), seeded"),
+}
+
+# FP64 FMA peak of one GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz
+# (nominal 1.25 TFLOP/s; an FMA-chain probe measured 1.251 TFLOP/s).  FP32: 128
+# FMA lanes per SM.
+PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+# DRAM traffic per launch (bytes) of the dominant kernel from one ncu capture,
+# valid only while the kernel sources hash to the recorded value.
+TRAFFIC = {}
+
+KERNEL_SOURCES = ["op_kernels.cuh", "op_elem.cuh", "op_launch.cuh", "vec_kernels.cu"]
+
+
+def kernel_src_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1806_01422_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def algorithmic_flops_per_element(op, d, n):
+    """Sum-factorised FLOPs of one element (naive n-term contractions, 2 flop per multiply-add).
+
+    F : 2d^2 contractions (d gradients and d divergences per component) + advection (2d flop per
+        node and component) + the subtraction (1);  J, J^T: 3d^2 contractions + 4d^2 + d per node.
+    """
+    contr = 2 * n ** (d + 1)
+    if op == "rhs":
+        return 2 * d * d * contr + (2 * d * d + d) * n ** d
+    return 3 * d * d * contr + (4 * d * d + d) * n ** d
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (getattr(self, "out", "") or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) != 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[2:]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle leg
+def oracle_sample(workload, rk_steps):
+    """Time the FP64 CPU oracle on a gradient evaluation of `rk_steps` steps (child process)."""
+    import numpy as np
+    from oracle.sem import Grid
+    from oracle import rk as ork
+    from paper_1806_01422_gb300 import inputs
+    w = WORKLOADS[workload]
+    g = Grid(w["dim"], w["E"], w["N"], w["nu"])
+    x = g.coords()
+    u0, uo = inputs.workload_field(w["dim"], x, inputs.SEED_U0), inputs.workload_field(w["dim"], x, inputs.SEED_UOBS)
+    t0 = time.perf_counter()
+    J, lam, _ = ork.objective_and_gradient(g, u0, uo, w["dt"], rk_steps, w["scheme"])
+    t1 = time.perf_counter()
+    return {"seconds": t1 - t0, "rk_steps": rk_steps, "J": J, "finite": bool(np.isfinite(lam).all())}
+
+
+def run_oracle_child(workload, rk_steps):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-sample", workload, str(rk_steps)]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: %s" % r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(workload, target_s=15.0):
+    """Oracle gradient evaluations/s from a bounded sample, one core, scaled to the full horizon."""
+    w = WORKLOADS[workload]
+    probe = run_oracle_child(workload, 2)
+    per_step = max(probe["seconds"] / 2, 1e-6)
+    n = int(max(2, min(w["nsteps"], target_s / per_step)))
+    res = run_oracle_child(workload, n)
+    per_eval = res["seconds"] * w["nsteps"] / n
+    return {"value": 1.0 / per_eval, "unit": "gradient evals/s", "cores": 1, "kind": "oracle",
+            "sample": "%d of %d RK steps of one gradient evaluation (forward + misfit + adjoint), "
+                      "FP64 numpy oracle, one thread; time scaled by %d/%d" % (n, w["nsteps"], w["nsteps"], n),
+            "seconds": res["seconds"]}
+
+
+# ---------------------------------------------------------------- distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend=os.environ.get("BENCH_BACKEND", "nccl"))
+    return world, rank, local
+
+
+def max_over_ranks(value, world, device):
+    """Max of a float over all ranks (the slowest rank sets the job time)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- arms
+def reference_arm(args, world, rank):
+    """The oracle (the slow plain CPU program the path is checked against), as it stands."""
+    if rank != 0:
+        return None
+    w = WORKLOADS[args.workload]
+    n = args.oracle_rk_steps
+    for _ in range(args.warmup):
+        run_oracle_child(args.workload, n)
+    secs = [run_oracle_child(args.workload, n)["seconds"] for _ in range(args.steps)]
+    per_eval = statistics.mean(secs) * w["nsteps"] / n
+    value = 1.0 / per_eval
+    sample = ("each step: %d of %d RK steps of one gradient evaluation, FP64 numpy oracle, one thread; "
+              "time scaled by %d/%d" % (n, w["nsteps"], w["nsteps"], n))
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "gradient evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_eval * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": w["data"], "config": {"workload": w["desc"]},
+            "cpu_baseline": {"value": value, "unit": "gradient evals/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "gradient evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def gpu_arm(args, world, rank, local):
+    import torch
+    from paper_1806_01422_gb300 import Sem, inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = WORKLOADS[args.workload]
+    s = Sem(w["dim"], w["E"], w["N"], w["nu"], precision=args.precision, ckpt=w["ckpt"], ckpt_slots=w["slots"],
+            device=dev)
+    x = s.coords()
+    u0_h = torch.from_numpy(inputs.workload_field(w["dim"], x, inputs.SEED_U0)).pin_memory()
+    uo_h = torch.from_numpy(inputs.workload_field(w["dim"], x, inputs.SEED_UOBS)).pin_memory()
+    u0, uo = u0_h.to(dev), uo_h.to(dev)
+    grad = s.empty()
+    nsteps, dt, scheme = w["nsteps"], w["dt"], w["scheme"]
+
+    def step():
+        return s.objective_grad(u0, uo, dt, nsteps, scheme, grad=grad)
+
+    for _ in range(args.warmup):
+        J, _ = step()
+    s.profile_read(reset=True)
+    s.profile(args.profile_every)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(args.steps):
+            J, _ = step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+    s.profile(0)
+    prof = s.profile_read(reset=True)
+    st = s.sweep_stats()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    tmax = max_over_ranks(elapsed, world, dev)
+    value = world * args.steps / tmax
+    # element kernel + assembly per apply, plus misfit, partial sum and adjoint seed per step
+    launches = args.steps * (2 * (st["forward_rhs"] + st["adjoint_rhs"] + st["adjoint_jacT"]) + 3)
+
+    # dominant kernel of the timed region and its roofline
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dom_ms, dom_n = kinds[dom]
+    avg_s = dom_ms / dom_n / 1e3
+    n = w["N"] + 1
+    nelem = w["E"] ** w["dim"]
+    fp32 = args.precision == "fp32_bulk"
+    names = {"rhs": "rhs", "jac": "jac", "jacT": "jact"}
+    if dom == "assemble":
+        # gather-scatter: reads n^d/N^d element-local values and writes one double per unique DOF
+        vb = 4 if fp32 else 8
+        bytes_per = s.ndof * ((n / w["N"]) ** w["dim"] * vb + 8)
+        achieved = bytes_per / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": args.hbm_peak, "unit": "GB/s",
+                "frac": achieved / args.hbm_peak, "kernel": "assemble_kernel"}
+    else:
+        flops = algorithmic_flops_per_element(dom, w["dim"], n) * nelem
+        achieved = flops / avg_s / 1e12
+        peak = PEAK_FP32_TFLOPS if fp32 else PEAK_FP64_TFLOPS
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "kernel": "%s%d_kernel<%s,%d>" % (names[dom], w["dim"], "float" if fp32 else "double", n)}
+    key = "%s@%s@%s" % (roof["kernel"], args.workload, args.precision)
+    tr = TRAFFIC.get(key)
+    roof["traffic"] = tr["bytes"] if tr and tr["src"] == kernel_src_hash() else None
+    roof["avg_launch_us"] = avg_s * 1e6
+    roof["timed_launches"] = dom_n
+    roof["timing"] = "CUDA events around 1 in %d launches of each kernel kind, on the launching stream, " \
+                     "inside the timed region" % args.profile_every
+
+    out = {"metric": METRIC, "value": value, "unit": "gradient evals/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": w["data"],
+           "config": {"workload": w["desc"], "dim": w["dim"], "E": w["E"], "N": w["N"], "unknowns": s.ndof,
+                      "scheme": scheme, "dt": dt, "rk_steps": nsteps, "trajectory": w["ckpt"],
+                      "precision": args.precision, "parallelism": "replicas" if world > 1 else "single GPU",
+                      "l2": "inputs larger than L2: every step writes and re-reads the stored stage trajectory "
+                            "(%.1f GB)" % (nsteps * 3 * s.ndof * 8 / 1e9 if w["ckpt"] == "stages" else 0.0)},
+           "roofline": roof, "gpu_launches": launches, "clocks": clk.summary(), "J": J,
+           "kernel_ms_per_step": {k: v[0] * args.profile_every / args.steps for k, v in prof.items()}}
+
+    if rank == 0 and not args.no_extras:
+        out.update(extras(s, u0, uo, w, dev))
+        # end to end through the public API with host buffers (pinned), copies inside the timed region
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            Jh, gh = s.objective_grad(u0_h, uo_h, dt, nsteps, scheme, host=True)
+        t1 = time.perf_counter()
+        out["e2e"] = {"value": args.steps / (t1 - t0), "unit": "gradient evals/s",
+                      "h2d_bytes_per_step": 2 * s.ndof * 8, "d2h_bytes_per_step": s.ndof * 8 + 8}
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
+    return out if rank == 0 else None
+
+
+def extras(s, u0, uo, w, dev):
+    """Standalone operator throughput and the forward/adjoint split (outside the timed region)."""
+    import torch
+    stream = torch.cuda.current_stream(dev)
+    out = s.empty()
+
+    def time_ms(fn, reps=30, warm=5):
+        for _ in range(warm):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps
+
+    tf = time_ms(lambda: s.rhs(u0, out))
+    tt = time_ms(lambda: s.jacT(u0, uo, out))
+    uN = s.empty()
+    lam = s.empty()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    torch.cuda.synchronize(dev)
+    e[0].record(stream)
+    s.rk_forward(u0, w["dt"], w["nsteps"], w["scheme"], out=uN)
+    e[1].record(stream)
+    s.objective(uN, uo, lam)
+    s.rk_adjoint(lam, out=lam)
+    e[2].record(stream)
+    torch.cuda.synchronize(dev)
+    fwd, adj = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    return {"gdofs_F": s.ndof / tf / 1e6, "gdofs_JT": s.ndof / tt / 1e6, "JT_over_F_apply": tt / tf,
+            "forward_ms": fwd, "adjoint_ms": adj, "adjoint_forward_ratio": adj / fwd}
+
+
+def ops_once(dim, E, N, precision):
+    """One F and one J^T apply (for ncu captures of the element and assembly kernels)."""
+    import torch
+    from paper_1806_01422_gb300 import Sem, inputs
+    s = Sem(dim, E, N, 1e-3, precision=precision)
+    x = s.coords()
+    u = torch.from_numpy(inputs.workload_field(dim, x, inputs.SEED_U0)).cuda()
+    v = torch.from_numpy(inputs.workload_field(dim, x, inputs.SEED_UOBS)).cuda()
+    out = s.empty()
+    s.rhs(u, out)
+    s.jacT(u, v, out)
+    torch.cuda.synchronize()
+    print(json.dumps({"ops_once": [dim, E, N, precision], "unknowns": s.ndof}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk"])
+    ap.add_argument("--hbm-peak", type=float, default=None, help="GB/s; default: MEASURED_PEAKS.json")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--oracle-rk-steps", type=int, default=10)
+    ap.add_argument("--rk-steps", type=int, default=None,
+                    help="override the workload's RK step count (profiling runs only; not a bench number)")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--profile-every", type=int, default=16, help="time one launch in this many per kernel kind")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-sample", nargs=2, metavar=("WORKLOAD", "RK_STEPS"), help=argparse.SUPPRESS)
+    ap.add_argument("--ops-once", nargs=4, metavar=("DIM", "E", "N", "PRECISION"),
+                    help="profiling driver: one F and one J^T apply on the workload field of that size, no timing")
+    args = ap.parse_args()
+
+    if args.oracle_sample:
+        print(json.dumps(oracle_sample(args.oracle_sample[0], int(args.oracle_sample[1]))))
+        return
+    if args.ops_once:
+        ops_once(int(args.ops_once[0]), int(args.ops_once[1]), int(args.ops_once[2]), args.ops_once[3])
+        return
+    if args.rk_steps:
+        for w in WORKLOADS.values():
+            w["nsteps"] = args.rk_steps
+    if args.hbm_peak is None:
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+                args.hbm_peak = float(json.load(fh)["hbm_gbs"])
+        except (OSError, KeyError, ValueError):
+            args.hbm_peak = 6800.0
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        res = reference_arm(args, world, rank)
+    else:
+        res = gpu_arm(args, world, rank, local)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -57,9 +57,10 @@ typedef struct sem_ctx* sem_t;
 
 /* arithmetic of the element kernels */
 #define SEM_PREC_FP64       0  /* everything in FP64 */
-#define SEM_PREC_FP32_BULK  1  /* FP32 contractions and pointwise products; FP64
-                                  gather-scatter sums, RK stage accumulation,
-                                  objective and adjoint accumulation */
+#define SEM_PREC_FP32_BULK  1  /* FP32 contractions, pointwise products and sums of
+                                  the <= 2^d element contributions per node; FP64
+                                  RK stage accumulation, objective and adjoint
+                                  accumulation */
 
 /* trajectory storage for the adjoint sweep (Sec. 5.3, Sec. 5.4) */
 #define SEM_CKPT_AUTO      0  /* STAGES if it fits ckpt_budget_bytes, else STATES, else BINOMIAL */
@@ -149,14 +150,14 @@ int sem_ckpt_plan(int nsteps, int slots, long long* advances);
 int sem_sweep_stats(sem_t h, long long* out3);
 
 /* Opt-in kernel timing (no counterpart in the paper; used by the benchmarks).
- * While enabled, every kernel launch of an operator apply on this handle is
- * bracketed by a pair of CUDA events on its stream.  sem_profile_read waits for
- * the recorded events and returns the summed device time in ms (ms4) and the
- * launch count (count4) per kind: [0] F element kernel, [1] J element kernel,
- * [2] J^T element kernel, [3] gather-scatter assembly; reset != 0 clears them.
- * Enabling costs two event records per launch and a stream wait every 4096
- * launches. */
-int sem_profile(sem_t h, int enable);
+ * With every = n > 0, one launch in n of each kind on this handle is bracketed
+ * by a pair of CUDA events on its stream (every = 0 turns timing off).
+ * sem_profile_read waits for the recorded events and returns the summed device
+ * time in ms (ms4) and the number of timed launches (count4) per kind:
+ * [0] F element kernel, [1] J element kernel, [2] J^T element kernel,
+ * [3] gather-scatter assembly; reset != 0 clears them.  Each timed launch costs
+ * two event records; the stream waits once per 4096 timed launches. */
+int sem_profile(sem_t h, int every);
 int sem_profile_read(sem_t h, double* ms4, long long* count4, int reset);
 
 /* Thread-local text of the last error ("" if none). */

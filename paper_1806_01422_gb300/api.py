@@ -128,11 +128,12 @@ class Sem:
                                            _stream(self.device)))
         return J.value, (grad.cpu() if host else grad)
 
-    def profile(self, enable=True):
-        L.check(L.lib().sem_profile(self._h, 1 if enable else 0))
+    def profile(self, every=1):
+        """Time one launch in `every` per kernel kind (0: off)."""
+        L.check(L.lib().sem_profile(self._h, int(every)))
 
     def profile_read(self, reset=True):
-        """{kind: (ms, launches)} for kinds rhs, jac, jacT element kernels and assembly."""
+        """{kind: (ms, timed launches)} for kinds rhs, jac, jacT element kernels and assembly."""
         ms = (ctypes.c_double * 4)()
         n = (ctypes.c_longlong * 4)()
         L.check(L.lib().sem_profile_read(self._h, ms, n, 1 if reset else 0))

@@ -22,52 +22,83 @@ __host__ __device__ constexpr int tiles_per_elem(int op) {
 }
 
 // ------------------------------------------------------------------ loaders
+// In the FP32 form each element tile of U (and W) holds U - U_ref, with U_ref
+// the value at the element's first node, formed in FP64 before rounding to
+// FP32.  The 1D matrices annihilate constants (Dhat 1 = 0), so gradients see
+// only the small in-element variation and lose far less to FP32 cancellation;
+// pointwise products add U_ref back.  The FP64 form stores U itself (ref = 0).
+template <typename T>
+struct RefSub {
+    static constexpr bool on = sizeof(T) == 4;
+};
+
+template <typename T>
+__device__ __forceinline__ T with_ref(T ref, T x) {
+    if constexpr (RefSub<T>::on) return ref + x;
+    else return x;
+}
+
 // Load component c of a global field into an element tile (d = 3): thread t of
 // the element owns column (i, j) = (t % n, t / n) and walks k.  `scale_mult`
 // multiplies each node by 1/k (k = elements sharing it), used for Z = v / k.
+// Returns the reference value subtracted from the tile (0 unless FP32 and not Z).
 template <typename T, int NP>
-__device__ __forceinline__ void load3(T* tile, const double* __restrict__ g, int c, int ex, int ey,
-                                      int ez, int t, bool valid, const ElemArgs& a, bool scale_mult) {
+__device__ __forceinline__ T load3(T* tile, const double* __restrict__ g, int c, int ex, int ey,
+                                   int ez, int t, bool valid, const ElemArgs& a, bool scale_mult) {
     using Tl = Tile<NP>;
     const int i = t % NP, j = t / NP;
     const int N = a.N, G = a.G;
     const int gx = wrap(ex * N + i, G), gy = wrap(ey * N + j, G);
     const bool bij = (i == 0 || i == N), bj = (j == 0 || j == N);
     const T sij = scale_mult ? (T)((bij ? 0.5 : 1.0) * (bj ? 0.5 : 1.0)) : (T)1;
+    double ref = 0.0;
+    if (RefSub<T>::on && !scale_mult && valid) ref = __ldg(g + gidx3(c, ez * N, ey * N, ex * N, G));
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
         const int gz = wrap(ez * N + k, G);
         T v = (T)0;
         if (valid) {
-            v = (T)__ldg(g + gidx3(c, gz, gy, gx, G));
-            const T sk = (scale_mult && (k == 0 || k == N)) ? (T)0.5 : (T)1;
-            v = v * sij * sk;
+            const double x = __ldg(g + gidx3(c, gz, gy, gx, G));
+            if (RefSub<T>::on && !scale_mult) {
+                v = (T)(x - ref);
+            } else {
+                v = (T)x;
+                if (scale_mult) v = v * sij * ((k == 0 || k == N) ? (T)0.5 : (T)1);
+            }
         }
         tile[(k * NP + j) * Tl::P + i] = v;
     }
+    return (T)ref;
 }
 
 // d = 2: thread t owns row j = t and walks i.
 template <typename T, int NP>
-__device__ __forceinline__ void load2(T* tile, const double* __restrict__ g, int c, int ex, int ey,
-                                      int t, bool valid, const ElemArgs& a, bool scale_mult) {
+__device__ __forceinline__ T load2(T* tile, const double* __restrict__ g, int c, int ex, int ey,
+                                   int t, bool valid, const ElemArgs& a, bool scale_mult) {
     using Tl = Tile<NP>;
     const int j = t;
     const int N = a.N, G = a.G;
     const int gy = wrap(ey * N + j, G);
     const T sj = (scale_mult && (j == 0 || j == N)) ? (T)0.5 : (T)1;
     const size_t row = ((size_t)c * G + gy) * G;
+    double ref = 0.0;
+    if (RefSub<T>::on && !scale_mult && valid) ref = __ldg(g + ((size_t)c * G + ey * N) * G + ex * N);
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
         const int gx = wrap(ex * N + i, G);
         T v = (T)0;
         if (valid) {
-            v = (T)__ldg(g + row + gx);
-            const T si = (scale_mult && (i == 0 || i == N)) ? (T)0.5 : (T)1;
-            v = v * sj * si;
+            const double x = __ldg(g + row + gx);
+            if (RefSub<T>::on && !scale_mult) {
+                v = (T)(x - ref);
+            } else {
+                v = (T)x;
+                if (scale_mult) v = v * sj * ((i == 0 || i == N) ? (T)0.5 : (T)1);
+            }
         }
         tile[j * Tl::P + i] = v;
     }
+    return (T)ref;
 }
 
 // ================================================================== d = 3
@@ -89,8 +120,9 @@ __global__ void rhs3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
     T* sG1 = sm + 4 * S3;
     T* sF = sm + 5 * S3;
     const int ex = e % a.E, ey = (e / a.E) % a.E, ez = e / (a.E * a.E);
+    T rU[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) load3<T, NP>(sU[c], a.u, c, ex, ey, ez, t, valid, a, false);
+    for (int c = 0; c < 3; ++c) rU[c] = load3<T, NP>(sU[c], a.u, c, ex, ey, ez, t, valid, a, false);
     __syncthreads();
     const int xb = t * P, yb = (t / NP) * S2 + t % NP, zb = (t / NP) * P + t % NP;
     T* out = reinterpret_cast<T*>(a.lvec) + (size_t)e * 3 * (NP * NP * NP);
@@ -115,9 +147,9 @@ __global__ void rhs3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
 #pragma unroll
             for (int m = 0; m < NP; ++m) {
                 const int id = zb + m * S2;
-                T adv = sU[0][id] * sG0[id];
-                adv = fma(sU[1][id], sG1[id], adv);
-                adv = fma(sU[2][id], gz[m], adv);
+                T adv = with_ref(rU[0], sU[0][id]) * sG0[id];
+                adv = fma(with_ref(rU[1], sU[1][id]), sG1[id], adv);
+                adv = fma(with_ref(rU[2], sU[2][id]), gz[m], adv);
                 f[m] -= adv;
             }
             st_line<T, NP, S2>(sF, zb, f);
@@ -162,10 +194,11 @@ __global__ void jac3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
     T* sF = sm + 8 * S3;
     T* sA = sm + 9 * S3;
     const int ex = e % a.E, ey = (e / a.E) % a.E, ez = e / (a.E * a.E);
+    T rU[3], rW[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        load3<T, NP>(sU[c], a.u, c, ex, ey, ez, t, valid, a, false);
-        load3<T, NP>(sW[c], a.w, c, ex, ey, ez, t, valid, a, false);
+        rU[c] = load3<T, NP>(sU[c], a.u, c, ex, ey, ez, t, valid, a, false);
+        rW[c] = load3<T, NP>(sW[c], a.w, c, ex, ey, ez, t, valid, a, false);
     }
     __syncthreads();
     const int xb = t * P, yb = (t / NP) * S2 + t % NP, zb = (t / NP) * P + t % NP;
@@ -181,7 +214,8 @@ __global__ void jac3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
             ld_line<T, NP, 1>(sU[c], xb, x);
             eo_apply<T, NP>(M.Dg, x, gu);
 #pragma unroll
-            for (int m = 0; m < NP; ++m) f[m] = -fma(sW[0][xb + m], gu[m], sU[0][xb + m] * gw[m]);
+            for (int m = 0; m < NP; ++m)
+                f[m] = -fma(with_ref(rW[0], sW[0][xb + m]), gu[m], with_ref(rU[0], sU[0][xb + m]) * gw[m]);
             st_line<T, NP, 1>(sF, xb, f);
             // y: gradient of W_c to sG1, advection y-term to sA
             ld_line<T, NP, P>(sW[c], yb, x);
@@ -192,7 +226,7 @@ __global__ void jac3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
 #pragma unroll
             for (int m = 0; m < NP; ++m) {
                 const int id = yb + m * P;
-                f[m] = -fma(sW[1][id], gu[m], sU[1][id] * gw[m]);
+                f[m] = -fma(with_ref(rW[1], sW[1][id]), gu[m], with_ref(rU[1], sU[1][id]) * gw[m]);
             }
             st_line<T, NP, P>(sA, yb, f);
         }
@@ -207,7 +241,7 @@ __global__ void jac3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
 #pragma unroll
             for (int m = 0; m < NP; ++m) {
                 const int id = zb + m * S2;
-                const T adv = fma(sW[2][id], gu[m], sU[2][id] * gw[m]);
+                const T adv = fma(with_ref(rW[2], sW[2][id]), gu[m], with_ref(rU[2], sU[2][id]) * gw[m]);
                 f[m] = (f[m] - adv) + (sF[id] + sA[id]);
             }
             st_line<T, NP, S2>(sF, zb, f);
@@ -251,9 +285,10 @@ __global__ void jact3_kernel(const __grid_constant__ OpMats<T, NP> M, const Elem
     T* sG1 = sm + 7 * S3;
     T* sF = sm + 8 * S3;
     const int ex = e % a.E, ey = (e / a.E) % a.E, ez = e / (a.E * a.E);
+    T rU[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        load3<T, NP>(sU[c], a.u, c, ex, ey, ez, t, valid, a, false);
+        rU[c] = load3<T, NP>(sU[c], a.u, c, ex, ey, ez, t, valid, a, false);
         load3<T, NP>(sZ[c], a.w, c, ex, ey, ez, t, valid, a, true);
     }
     __syncthreads();
@@ -268,7 +303,7 @@ __global__ void jact3_kernel(const __grid_constant__ OpMats<T, NP> M, const Elem
             ld_line<T, NP, 1>(sZl, xb, z);
             eo_apply<T, NP>(M.Vz, z, q);
 #pragma unroll
-            for (int m = 0; m < NP; ++m) q[m] = fma(sU[0][xb + m], z[m], q[m]);
+            for (int m = 0; m < NP; ++m) q[m] = fma(with_ref(rU[0], sU[0][xb + m]), z[m], q[m]);
             st_line<T, NP, 1>(sG0, xb, q);
             if (l == 0) {  // reaction term along x: -sum_c Z_c Dg_x U_c
                 T acc[NP], x[NP], g[NP];
@@ -289,7 +324,7 @@ __global__ void jact3_kernel(const __grid_constant__ OpMats<T, NP> M, const Elem
             ld_line<T, NP, P>(sZl, yb, z);
             eo_apply<T, NP>(M.Vz, z, q);
 #pragma unroll
-            for (int m = 0; m < NP; ++m) q[m] = fma(sU[1][yb + m * P], z[m], q[m]);
+            for (int m = 0; m < NP; ++m) q[m] = fma(with_ref(rU[1], sU[1][yb + m * P]), z[m], q[m]);
             st_line<T, NP, P>(sG1, yb, q);
             if (l == 1) {
                 T acc[NP], x[NP], g[NP];
@@ -313,7 +348,7 @@ __global__ void jact3_kernel(const __grid_constant__ OpMats<T, NP> M, const Elem
             ld_line<T, NP, S2>(sZl, zb, z);
             eo_apply<T, NP>(M.Vz, z, q);
 #pragma unroll
-            for (int m = 0; m < NP; ++m) q[m] = fma(sU[2][zb + m * S2], z[m], q[m]);
+            for (int m = 0; m < NP; ++m) q[m] = fma(with_ref(rU[2], sU[2][zb + m * S2]), z[m], q[m]);
             eo_apply<T, NP>(M.Dd, q, f);
             if (l == 2) {
                 T x[NP], g[NP];
@@ -371,8 +406,9 @@ __global__ void rhs2_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
     T* sG1 = sm + 2 * S2;
     T* sF = sm + 3 * S2;
     const int ex = e % a.E, ey = e / a.E;
+    T rU[2];
 #pragma unroll
-    for (int c = 0; c < 2; ++c) load2<T, NP>(sU[c], a.u, c, ex, ey, t, valid, a, false);
+    for (int c = 0; c < 2; ++c) rU[c] = load2<T, NP>(sU[c], a.u, c, ex, ey, t, valid, a, false);
     __syncthreads();
     const int xb = t * P, yb = t;
     T* out = reinterpret_cast<T*>(a.lvec) + (size_t)e * 2 * (NP * NP);
@@ -393,7 +429,7 @@ __global__ void rhs2_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
 #pragma unroll
             for (int m = 0; m < NP; ++m) {
                 const int id = xb + m;
-                const T adv = fma(sU[1][id], sG1[id], sU[0][id] * gx[m]);
+                const T adv = fma(with_ref(rU[1], sU[1][id]), sG1[id], with_ref(rU[0], sU[0][id]) * gx[m]);
                 f[m] -= adv;
             }
             st_line<T, NP, 1>(sF, xb, f);
@@ -428,10 +464,11 @@ __global__ void jac2_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
     T* sG1 = sm + 4 * S2;
     T* sF = sm + 5 * S2;
     const int ex = e % a.E, ey = e / a.E;
+    T rU[2], rW[2];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-        load2<T, NP>(sU[c], a.u, c, ex, ey, t, valid, a, false);
-        load2<T, NP>(sW[c], a.w, c, ex, ey, t, valid, a, false);
+        rU[c] = load2<T, NP>(sU[c], a.u, c, ex, ey, t, valid, a, false);
+        rW[c] = load2<T, NP>(sW[c], a.w, c, ex, ey, t, valid, a, false);
     }
     __syncthreads();
     const int xb = t * P, yb = t;
@@ -448,7 +485,7 @@ __global__ void jac2_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
 #pragma unroll
             for (int m = 0; m < NP; ++m) {
                 const int id = yb + m * P;
-                f[m] = -fma(sW[1][id], gu[m], sU[1][id] * gw[m]);
+                f[m] = -fma(with_ref(rW[1], sW[1][id]), gu[m], with_ref(rU[1], sU[1][id]) * gw[m]);
             }
             st_line<T, NP, P>(sF, yb, f);
         }
@@ -463,7 +500,7 @@ __global__ void jac2_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
 #pragma unroll
             for (int m = 0; m < NP; ++m) {
                 const int id = xb + m;
-                const T adv = fma(sW[0][id], gu[m], sU[0][id] * gw[m]);
+                const T adv = fma(with_ref(rW[0], sW[0][id]), gu[m], with_ref(rU[0], sU[0][id]) * gw[m]);
                 f[m] = (f[m] - adv) + sF[id];
             }
             st_line<T, NP, 1>(sF, xb, f);
@@ -498,9 +535,10 @@ __global__ void jact2_kernel(const __grid_constant__ OpMats<T, NP> M, const Elem
     T* sG1 = sm + 4 * S2;
     T* sF = sm + 5 * S2;
     const int ex = e % a.E, ey = e / a.E;
+    T rU[2];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-        load2<T, NP>(sU[c], a.u, c, ex, ey, t, valid, a, false);
+        rU[c] = load2<T, NP>(sU[c], a.u, c, ex, ey, t, valid, a, false);
         load2<T, NP>(sZ[c], a.w, c, ex, ey, t, valid, a, true);
     }
     __syncthreads();
@@ -513,7 +551,7 @@ __global__ void jact2_kernel(const __grid_constant__ OpMats<T, NP> M, const Elem
             ld_line<T, NP, P>(sZ[l], yb, z);
             eo_apply<T, NP>(M.Vz, z, q);
 #pragma unroll
-            for (int m = 0; m < NP; ++m) q[m] = fma(sU[1][yb + m * P], z[m], q[m]);
+            for (int m = 0; m < NP; ++m) q[m] = fma(with_ref(rU[1], sU[1][yb + m * P]), z[m], q[m]);
             st_line<T, NP, P>(sG1, yb, q);
             if (l == 1) {
                 T acc[NP], x[NP], g[NP];
@@ -537,7 +575,7 @@ __global__ void jact2_kernel(const __grid_constant__ OpMats<T, NP> M, const Elem
             ld_line<T, NP, 1>(sZ[l], xb, z);
             eo_apply<T, NP>(M.Vz, z, q);
 #pragma unroll
-            for (int m = 0; m < NP; ++m) q[m] = fma(sU[0][xb + m], z[m], q[m]);
+            for (int m = 0; m < NP; ++m) q[m] = fma(with_ref(rU[0], sU[0][xb + m]), z[m], q[m]);
             eo_apply<T, NP>(M.Dd, q, f);
             if (l == 0) {
                 T x[NP], g[NP];
@@ -573,14 +611,20 @@ __global__ void jact2_kernel(const __grid_constant__ OpMats<T, NP> M, const Elem
 // ================================================================== d = 1
 // One thread per element; everything in registers.
 template <typename T, int NP>
-__device__ __forceinline__ void load1(T (&x)[NP], const double* __restrict__ g, int e, const ElemArgs& a,
-                                      bool scale_mult) {
+__device__ __forceinline__ T load1(T (&x)[NP], const double* __restrict__ g, int e, const ElemArgs& a,
+                                   bool scale_mult) {
+    const double ref = (RefSub<T>::on && !scale_mult) ? __ldg(g + wrap(e * a.N, a.G)) : 0.0;
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-        T v = (T)__ldg(g + wrap(e * a.N + i, a.G));
-        if (scale_mult && (i == 0 || i == a.N)) v *= (T)0.5;
-        x[i] = v;
+        const double v = __ldg(g + wrap(e * a.N + i, a.G));
+        if (RefSub<T>::on && !scale_mult) {
+            x[i] = (T)(v - ref);
+        } else {
+            x[i] = (T)v;
+            if (scale_mult && (i == 0 || i == a.N)) x[i] *= (T)0.5;
+        }
     }
+    return (T)ref;
 }
 
 template <typename T, int NP>
@@ -588,27 +632,27 @@ __global__ void op1_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemAr
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= a.nelem) return;
     T u[NP], f[NP];
-    load1<T, NP>(u, a.u, e, a, false);
+    const T ru = load1<T, NP>(u, a.u, e, a, false);
     if (op == OP_RHS) {
         T g[NP];
         eo_apply<T, NP>(M.Dg, u, g);
         eo_apply<T, NP>(M.Dv, g, f);
 #pragma unroll
-        for (int m = 0; m < NP; ++m) f[m] = fma(-u[m], g[m], f[m]);
+        for (int m = 0; m < NP; ++m) f[m] = fma(-with_ref(ru, u[m]), g[m], f[m]);
     } else if (op == OP_JAC) {
         T w[NP], gu[NP], gw[NP];
-        load1<T, NP>(w, a.w, e, a, false);
+        const T rw = load1<T, NP>(w, a.w, e, a, false);
         eo_apply<T, NP>(M.Dg, u, gu);
         eo_apply<T, NP>(M.Dg, w, gw);
         eo_apply<T, NP>(M.Dv, gw, f);
 #pragma unroll
-        for (int m = 0; m < NP; ++m) f[m] -= fma(w[m], gu[m], u[m] * gw[m]);
+        for (int m = 0; m < NP; ++m) f[m] -= fma(with_ref(rw, w[m]), gu[m], with_ref(ru, u[m]) * gw[m]);
     } else {
         T z[NP], q[NP], gu[NP];
         load1<T, NP>(z, a.w, e, a, true);
         eo_apply<T, NP>(M.Vz, z, q);
 #pragma unroll
-        for (int m = 0; m < NP; ++m) q[m] = fma(u[m], z[m], q[m]);
+        for (int m = 0; m < NP; ++m) q[m] = fma(with_ref(ru, u[m]), z[m], q[m]);
         eo_apply<T, NP>(M.Dd, q, f);
         eo_apply<T, NP>(M.Dg, u, gu);
 #pragma unroll

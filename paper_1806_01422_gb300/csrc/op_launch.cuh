@@ -23,6 +23,7 @@ void split_eo(EOMat<T, NP>& M, const double* A) {
 }
 
 constexpr int SMEM_TARGET = 100 * 1024;   // two blocks per SM fit in 227 KB
+constexpr int NUM_SMS = 152;               // GB300: 2 dies x 76 SMs
 
 template <typename T, int D, int NP>
 size_t elem_smem_bytes(int op) {
@@ -47,8 +48,12 @@ cudaError_t launch_elem_np(int op, const double* mats, const ElemArgs& a, cudaSt
     } else {
         constexpr int TPE = D == 3 ? NP * NP : NP;
         const size_t per = elem_smem_bytes<T, D, NP>(op);
-        int epb = std::max(1, std::min(256 / TPE, (int)(SMEM_TARGET / per)));
-        epb = std::min(epb, a.nelem);
+        const int epb_max = std::max(1, std::min(256 / TPE, (int)(SMEM_TARGET / per)));
+        // Balance the grid over the SMs: the fewest waves k of NUM_SMS blocks that
+        // fit epb_max elements per block, then the smallest block that fills them.
+        const int waves = (a.nelem + NUM_SMS * epb_max - 1) / (NUM_SMS * epb_max);
+        int epb = (a.nelem + NUM_SMS * waves - 1) / (NUM_SMS * waves);
+        epb = std::max(1, std::min(epb, epb_max));
         const size_t smem = per * epb;
         if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
         const int threads = epb * TPE;

@@ -103,7 +103,8 @@ struct sem_ctx {
     std::vector<int> f_ckpt;
     long long st[3] = {0, 0, 0};  // forward F applies, adjoint F applies, adjoint J^T applies
     // opt-in kernel timing: event pairs per launch, drained when the pool fills
-    bool prof = false;
+    int prof = 0;                 // 0: off; n: time one apply in n per kind
+    long long prof_tick[4] = {0, 0, 0, 0};
     std::vector<cudaEvent_t> ev_start, ev_stop;
     std::vector<int> ev_kind;
     size_t ev_used = 0;
@@ -195,6 +196,7 @@ int prof_drain(sem_t h) {
 int prof_begin(sem_t h, int kind, cudaStream_t s, long long& slot) {
     slot = -1;
     if (!h->prof) return SEM_OK;
+    if (h->prof_tick[kind]++ % h->prof != 0) return SEM_OK;
     if (h->ev_start.empty()) {
         h->ev_start.resize(PROF_POOL);
         h->ev_stop.resize(PROF_POOL);
@@ -716,10 +718,11 @@ int sem_sweep_stats(sem_t h, long long* out3) {
     return SEM_OK;
 }
 
-int sem_profile(sem_t h, int enable) {
-    if (!h) return fail(SEM_ERR_ARG, "null handle");
-    if (!enable) SEM_TRY(prof_drain(h));
-    h->prof = enable != 0;
+int sem_profile(sem_t h, int every) {
+    if (!h || every < 0) return fail(SEM_ERR_ARG, "null handle or negative sampling period");
+    if (!every) SEM_TRY(prof_drain(h));
+    h->prof = every;
+    for (int i = 0; i < 4; ++i) h->prof_tick[i] = 0;
     return SEM_OK;
 }
 
@@ -742,3 +745,4 @@ const char* sem_last_error(void) { return g_err.c_str(); }
 }  // extern "C"
 
 int semk::max_np(int D, bool fp32) { return (D == 3 && !fp32) ? 12 : 16; }
+

@@ -5,6 +5,7 @@
 
 #include "op_kernels.cuh"
 
+
 namespace semk {
 
 // Element kernel launch for dimension D, compute type T, runtime point count
@@ -19,6 +20,8 @@ int max_np(int D, bool fp32);
 // --------------------------------------------------------------- assembly
 // Epilogue of the gather-scatter sum: for each unique scalar node with
 // assembled value a,  out[o] = alpha[o] a + sum_m beta[o][m] src[m]  (o < nout).
+// The host fills alpha; the launcher folds the 1/k multiplicity of F and J
+// into alpha_k[o][nsh] = alpha[o] / 2^nsh so the kernel spends one multiply.
 struct Epi {
     double* out[3];
     double alpha[3];
@@ -26,6 +29,7 @@ struct Epi {
     double beta[3][4];
     int nout, nsrc;
     unsigned* nonfinite;  // set to 1 if any output is NaN/Inf (may be null)
+    double alpha_k[3][4]; // filled by launch_assemble
 };
 
 struct AsmArgs {
@@ -33,6 +37,8 @@ struct AsmArgs {
     unsigned GD;       // G^D
     unsigned ndof;     // D * G^D
     int scale_mult;    // 1: multiply the sum by 1/k (F and J); 0: plain sum (J^T)
+    unsigned divN_mul; // g / N == (g * divN_mul) >> divN_shift for every 0 <= g < G (set by launch_assemble)
+    int divN_shift;
 };
 
 cudaError_t launch_assemble(bool lvec_fp32, const void* lvec, const AsmArgs& a, const Epi& ep,

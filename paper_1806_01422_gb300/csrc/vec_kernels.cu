@@ -14,75 +14,144 @@
 
 namespace semk {
 
+// FP64 work per unique node: (contributions - 1) adds, then per output one
+// multiply and one fused multiply-add per source.  The FP64 pipe of GB300 issues
+// two lanes per SM per clock, so everything else (the non-finite test on the
+// exponent bits, the choice of contributions, the index arithmetic) stays on the
+// integer pipes.
+__device__ __forceinline__ bool nonfinite_bits(double v) {
+    return (__double2hiint(v) & 0x7ff00000) == 0x7ff00000;
+}
+
+// The launch grid is (ceil(G / 128), G, d) for d = 2 and (ceil(G / 128), G, d G)
+// for d = 3, so a thread finds its node without integer division (32-bit
+// division and modulo issue conversion instructions on the FP64 pipe); the
+// element index along an axis is a multiply-shift checked on the host.
 template <typename T, int D>
-__global__ void __launch_bounds__(256) assemble_kernel(const T* __restrict__ lvec, const AsmArgs a,
+__global__ void __launch_bounds__(128) assemble_kernel(const T* __restrict__ lvec, const AsmArgs a,
                                                        const Epi ep) {
-    const unsigned stride = gridDim.x * blockDim.x;
+    int g[3];
+    int c;
+    g[0] = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g[0] >= a.G) return;
+    if (D == 1) {
+        c = 0;
+    } else if (D == 2) {
+        g[1] = blockIdx.y;
+        c = blockIdx.z;
+    } else {
+        g[1] = blockIdx.y;
+        c = blockIdx.z / a.G;          // once per block: blockIdx.z < 3G
+        g[2] = blockIdx.z - c * a.G;
+    }
+    unsigned idx = c * a.GD;
+    {
+        unsigned st = 1;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            idx += g[d] * st;
+            st *= a.G;
+        }
+    }
     int npd = a.NP;
     if (D >= 2) npd *= a.NP;
     if (D >= 3) npd *= a.NP;
-    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < a.ndof; idx += stride) {
-        const unsigned c = idx / a.GD;
-        unsigned r = idx - c * a.GD;
-        int e0[3], i0[3];
-        bool sh[3];
-        int nsh = 0;
+    int e0[3], e1[3], i0[3];
+    int shmask = 0, nsh = 0;
 #pragma unroll
-        for (int d = 0; d < D; ++d) {
-            const unsigned g = r % (unsigned)a.G;
-            r /= (unsigned)a.G;
-            e0[d] = (int)g / a.N;
-            i0[d] = (int)g - e0[d] * a.N;
-            sh[d] = (i0[d] == 0);
-            nsh += sh[d];
+    for (int d = 0; d < D; ++d) {
+        e0[d] = (int)(((unsigned)g[d] * a.divN_mul) >> a.divN_shift);
+        i0[d] = g[d] - e0[d] * a.N;
+        e1[d] = e0[d] == 0 ? a.E - 1 : e0[d] - 1;
+        if (i0[d] == 0) {
+            shmask |= 1 << d;
+            ++nsh;
         }
-        double sum = 0.0;
-#pragma unroll
-        for (int combo = 0; combo < (1 << D); ++combo) {
-            bool ok = true;
-            size_t el = 0;
-            int node = 0;
-#pragma unroll
-            for (int d = D - 1; d >= 0; --d) {
-                const int bit = (combo >> d) & 1;
-                if (bit && !sh[d]) ok = false;
-                const int ed = bit ? (e0[d] == 0 ? a.E - 1 : e0[d] - 1) : e0[d];
-                const int id = bit ? a.N : i0[d];
-                el = el * a.E + ed;
-                node = node * a.NP + id;
-            }
-            if (ok) sum += (double)lvec[(el * D + c) * (size_t)npd + node];
-        }
-        if (a.scale_mult) sum = ldexp(sum, -nsh);
-        // read every source before writing any output: an output may be a source (in place)
-        double sv[4];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) sv[m] = m < ep.nsrc ? ep.src[m][idx] : 0.0;
-        double ov[3];
-        bool bad = false;
-#pragma unroll
-        for (int o = 0; o < 3; ++o) {
-            if (o >= ep.nout) break;
-            double v = ep.alpha[o] * sum;
-#pragma unroll
-            for (int m = 0; m < 4; ++m)
-                if (m < ep.nsrc && ep.beta[o][m] != 0.0) v = fma(ep.beta[o][m], sv[m], v);
-            ov[o] = v;
-            bad |= !isfinite(v);
-        }
-#pragma unroll
-        for (int o = 0; o < 3; ++o)
-            if (o < ep.nout) ep.out[o][idx] = ov[o];
-        if (bad && ep.nonfinite) atomicOr(ep.nonfinite, 1u);
     }
+    // contributions in a fixed order: combo = bit pattern of the "left neighbour" choices
+    T sumT = (T)0;
+    double sum = 0.0;
+    bool first = true;
+#pragma unroll
+    for (int combo = 0; combo < (1 << D); ++combo) {
+        if (combo & ~shmask) continue;
+        unsigned el = 0, node = 0;
+#pragma unroll
+        for (int d = D - 1; d >= 0; --d) {
+            const bool bit = (combo >> d) & 1;
+            el = el * a.E + (bit ? e1[d] : e0[d]);
+            node = node * a.NP + (bit ? a.N : i0[d]);
+        }
+        const T v = lvec[((size_t)el * D + c) * (size_t)npd + node];
+        if constexpr (sizeof(T) == 8) {
+            sum = first ? (double)v : sum + (double)v;
+        } else {
+            sumT = first ? v : sumT + v;
+        }
+        first = false;
+    }
+    if constexpr (sizeof(T) != 8) sum = (double)sumT;
+    // read every source before writing any output: an output may be a source (in place)
+    double sv[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) sv[m] = m < ep.nsrc ? ep.src[m][idx] : 0.0;
+    double ov[3];
+    bool bad = false;
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+        if (o >= ep.nout) break;
+        double v = ep.alpha_k[o][nsh] * sum;
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            if (m < ep.nsrc) v = fma(ep.beta[o][m], sv[m], v);
+        ov[o] = v;
+        bad |= nonfinite_bits(v);
+    }
+#pragma unroll
+    for (int o = 0; o < 3; ++o)
+        if (o < ep.nout) ep.out[o][idx] = ov[o];
+    if (bad && ep.nonfinite) atomicOr(ep.nonfinite, 1u);
 }
 
-cudaError_t launch_assemble(bool lvec_fp32, const void* lvec, const AsmArgs& a, const Epi& ep,
+// Multiply-shift for g / N on 0 <= g < G, verified exhaustively (G <= 65535).
+static bool magic_div(int N, int G, unsigned& mul, int& shift) {
+    for (shift = 16; shift <= 31; ++shift) {
+        mul = (unsigned)(((1ull << shift) + N - 1) / N);
+        bool ok = true;
+        for (unsigned g = 0; g < (unsigned)G && ok; ++g)
+            ok = (unsigned)(((unsigned long long)g * mul) >> shift) == g / (unsigned)N &&
+                 (unsigned long long)g * mul < (1ull << 32);
+        if (ok) return true;
+    }
+    return false;
+}
+
+cudaError_t launch_assemble(bool lvec_fp32, const void* lvec, const AsmArgs& a_in, const Epi& ep_in,
                             cudaStream_t s) {
-    const int threads = 256;
-    const unsigned blocks = (a.ndof + threads - 1) / threads;
-    if (blocks == 0) return cudaSuccess;
-#define SEMK_ASM(T, D) assemble_kernel<T, D><<<blocks, threads, 0, s>>>((const T*)lvec, a, ep)
+    Epi ep = ep_in;
+    for (int o = 0; o < 3; ++o)
+        for (int k = 0; k < 4; ++k) ep.alpha_k[o][k] = a_in.scale_mult ? ep.alpha[o] / (double)(1 << k) : ep.alpha[o];
+    AsmArgs a = a_in;
+    if (a.G <= 0) return cudaSuccess;
+    thread_local int cN = -1, cG = -1, cShift = 0;
+    thread_local unsigned cMul = 0;
+    if (a.N != cN || a.G != cG) {
+        if (a.G > 65535 || !magic_div(a.N, a.G, cMul, cShift)) return cudaErrorInvalidValue;
+        cN = a.N;
+        cG = a.G;
+    }
+    a.divN_mul = cMul;
+    a.divN_shift = cShift;
+    const int threads = 128;
+    dim3 grid((a.G + threads - 1) / threads, 1, 1);
+    if (a.D == 2) {
+        grid.y = a.G;
+        grid.z = 2;
+    } else if (a.D == 3) {
+        grid.y = a.G;
+        grid.z = 3 * a.G;
+    }
+#define SEMK_ASM(T, D) assemble_kernel<T, D><<<grid, threads, 0, s>>>((const T*)lvec, a, ep)
     if (lvec_fp32) {
         if (a.D == 1) SEMK_ASM(float, 1);
         else if (a.D == 2) SEMK_ASM(float, 2);
