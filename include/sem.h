@@ -160,6 +160,22 @@ int sem_sweep_stats(sem_t h, long long* out3);
 int sem_profile(sem_t h, int every);
 int sem_profile_read(sem_t h, double* ms4, long long* count4, int reset);
 
+/* Size of the fixed device array used by sem_rhs_noalloc (16 MiB). */
+#define SEM_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+
+/* f = F(u) exactly as sem_rhs computes it, but without allocating any device
+ * memory (the paper has no counterpart; this serves callers that cannot call
+ * cudaMalloc, e.g. hosts whose device memory belongs to their own pool, or
+ * loops that must not take the synchronisation an allocation can cause).
+ * The element-local scratch is a file-scope device array of
+ * SEM_NOALLOC_SCRATCH_BYTES on every GPU that loads the library, kept until the
+ * process exits; grids needing more (d * E^d * (N+1)^d values of the compute
+ * type) return SEM_ERR_ARG.  The first call on a device looks the array up
+ * with that device current, so make it before any stream capture.  All calls
+ * share the array: calls whose kernels overlap on the GPU race and must be
+ * ordered by the caller.  Arguments and errors otherwise as sem_rhs. */
+int sem_rhs_noalloc(sem_t h, const double* u, double* f, void* stream);
+
 /* Thread-local text of the last error ("" if none). */
 const char* sem_last_error(void);
 

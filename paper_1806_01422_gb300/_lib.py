@@ -56,6 +56,7 @@ _SIGS = {
     "sem_sweep_stats": (_I, [_H, ctypes.POINTER(ctypes.c_longlong)]),
     "sem_profile": (_I, [_H, _I]),
     "sem_profile_read": (_I, [_H, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), _I]),
+    "sem_rhs_noalloc": (_I, [_H, _P, _P, _P]),
     "sem_last_error": (ctypes.c_char_p, []),
 }
 

@@ -746,3 +746,20 @@ const char* sem_last_error(void) { return g_err.c_str(); }
 
 int semk::max_np(int D, bool fp32) { return (D == 3 && !fp32) ? 12 : 16; }
 
+// Read-only view of a handle for entry points defined in other translation units.
+int semk::handle_view(sem_t h, HandleView* v) {
+    if (!h || !v) return SEM_ERR_ARG;
+    v->dim = h->dim;
+    v->E = h->E;
+    v->N = h->N;
+    v->G = h->G;
+    v->np = h->np;
+    v->nelem = h->nelem;
+    v->ndof = h->ndof;
+    v->lvec_elems = h->lvec_elems;
+    v->fp32 = h->precision == SEM_PREC_FP32_BULK;
+    v->mats = h->mats.data();
+    return SEM_OK;
+}
+
+void semk::set_error(const char* msg) { g_err = msg; }

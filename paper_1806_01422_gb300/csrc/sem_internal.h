@@ -5,6 +5,7 @@
 
 #include "op_kernels.cuh"
 
+struct sem_ctx;
 
 namespace semk {
 
@@ -58,6 +59,16 @@ cudaError_t launch_objective(const double* u, const double* uo, double* lam, dou
 cudaError_t launch_sum_partials(const double* partials, int n, double* out, double factor,
                                 cudaStream_t s);
 int objective_blocks(unsigned ndof);
+
+// Read-only view of a handle's grid and tables (for entry points outside sem_api.cu).
+struct HandleView {
+    int dim, E, N, G, np, nelem;
+    size_t ndof, lvec_elems;
+    bool fp32;
+    const double* mats;   // 4 x np x np element matrices
+};
+int handle_view(struct ::sem_ctx* h, HandleView* v);
+void set_error(const char* msg);
 
 // out <- alpha * in  (n doubles)
 cudaError_t launch_scale(double* out, const double* in, double alpha, size_t n, cudaStream_t s);
