@@ -37,6 +37,13 @@ WORKLOADS = {
                desc="3D vector viscous Burgers, periodic [0,1]^3, 32^3 hexes, N=7 (33,718,272 unknowns), "
                     "nu=5e-4, RK4 dt=2.5e-4 x 1000 steps, binomial checkpointing with 20 slots",
                data="synthetic: seeded random-phase fields, spectrum ~k^-5/3 cut at |k| = 16, max|u0| = 1"),
+    "batch": dict(dim=2, E=None, N=None, nu=1e-3, scheme="rk4", dt=1.5e-4, nsteps=300, ckpt="states", slots=0,
+                  count=256,
+                  desc="256 independent 2D vector viscous Burgers instances, periodic [0,1]^2, E per side drawn "
+                       "from {8,16,24,32,48} and N from {5,7,9} (seed 4), nu=1e-3, RK4 dt=1.5e-4 x 300 steps, "
+                       "one persistent launch per operator pass, every step's state stored (stages recomputed); one "
+                       "batched gradient evaluation per step (256 instance gradients)",
+                  data="synthetic: per instance k seeded 16-mode Fourier fields (seeds 1000+2k, 1001+2k)"),
     "1d": dict(dim=1, E=16, N=7, nu=0.01, scheme="rk4", dt=1e-3, nsteps=500, ckpt="stages", slots=0,
                desc="1D viscous Burgers, periodic [0,2pi), 16 elements, N=7 (112 unknowns), nu=0.01, "
                     "RK4 dt=1e-3 x 500 steps",
@@ -193,6 +200,12 @@ def max_over_ranks(value, world, device):
     return float(t.item())
 
 
+def job_value(per_rank_seconds, steps, world, device):
+    """Whole-job throughput: all ranks' steps over the slowest rank's time (weak scaling)."""
+    tmax = max_over_ranks(per_rank_seconds, world, device)
+    return world * steps / tmax, tmax
+
+
 def barrier(world):
     if world > 1:
         import torch.distributed as dist
@@ -229,11 +242,22 @@ def gpu_arm(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = WORKLOADS[args.workload]
-    s = Sem(w["dim"], w["E"], w["N"], w["nu"], precision=args.precision, ckpt=w["ckpt"], ckpt_slots=w["slots"],
-            device=dev)
-    x = s.coords()
-    u0_h = torch.from_numpy(inputs.workload_field(w["dim"], x, inputs.SEED_U0)).pin_memory()
-    uo_h = torch.from_numpy(inputs.workload_field(w["dim"], x, inputs.SEED_UOBS)).pin_memory()
+    if args.workload == "batch":
+        from paper_1806_01422_gb300 import SemBatch
+        Es, Ns = inputs.batch_shapes(w["count"])
+        s = SemBatch(Es, Ns, [w["nu"]] * w["count"], ckpt=w["ckpt"], device=dev)
+        u0_h = torch.from_numpy(s.pack([inputs.field_2d(s.coords(k), inputs.batch_seeds(k)[0])
+                                        for k in range(s.count)])).pin_memory()
+        uo_h = torch.from_numpy(s.pack([inputs.field_2d(s.coords(k), inputs.batch_seeds(k)[1])
+                                        for k in range(s.count)])).pin_memory()
+        units = w["count"]
+    else:
+        s = Sem(w["dim"], w["E"], w["N"], w["nu"], precision=args.precision, ckpt=w["ckpt"], ckpt_slots=w["slots"],
+                device=dev)
+        x = s.coords()
+        u0_h = torch.from_numpy(inputs.workload_field(w["dim"], x, inputs.SEED_U0)).pin_memory()
+        uo_h = torch.from_numpy(inputs.workload_field(w["dim"], x, inputs.SEED_UOBS)).pin_memory()
+        units = 1
     u0, uo = u0_h.to(dev), uo_h.to(dev)
     grad = s.empty()
     nsteps, dt, scheme = w["nsteps"], w["dt"], w["scheme"]
@@ -260,8 +284,7 @@ def gpu_arm(args, world, rank, local):
     prof = s.profile_read(reset=True)
     st = s.sweep_stats()
     elapsed = e0.elapsed_time(e1) / 1e3
-    tmax = max_over_ranks(elapsed, world, dev)
-    value = world * args.steps / tmax
+    value, tmax = job_value(elapsed, args.steps * units, world, dev)
     # element kernel + assembly per apply, plus misfit, partial sum and adjoint seed per step
     launches = args.steps * (2 * (st["forward_rhs"] + st["adjoint_rhs"] + st["adjoint_jacT"]) + 3)
 
@@ -270,23 +293,30 @@ def gpu_arm(args, world, rank, local):
     dom = max(kinds, key=lambda k: kinds[k][0])
     dom_ms, dom_n = kinds[dom]
     avg_s = dom_ms / dom_n / 1e3
-    n = w["N"] + 1
-    nelem = w["E"] ** w["dim"]
     fp32 = args.precision == "fp32_bulk"
     names = {"rhs": "rhs", "jac": "jac", "jacT": "jact"}
+    if args.workload == "batch":
+        shapes = list(zip(s.E, s.N))
+        kname = "batch_elem2_kernel"
+    else:
+        shapes = [(w["E"], w["N"])]
+        kname = None
     if dom == "assemble":
-        # gather-scatter: reads n^d/N^d element-local values and writes one double per unique DOF
+        # gather-scatter of one plain apply: reads the d E^d (N+1)^d element-local values and
+        # writes the d (E N)^d unknowns (the RK epilogue's sources are not counted)
         vb = 4 if fp32 else 8
-        bytes_per = s.ndof * ((n / w["N"]) ** w["dim"] * vb + 8)
+        d = w["dim"]
+        bytes_per = sum(d * (E * (N + 1)) ** d * vb + d * (E * N) ** d * 8 for E, N in shapes)
         achieved = bytes_per / avg_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": args.hbm_peak, "unit": "GB/s",
-                "frac": achieved / args.hbm_peak, "kernel": "assemble_kernel"}
+                "frac": achieved / args.hbm_peak, "kernel": "assemble kernel"}
     else:
-        flops = algorithmic_flops_per_element(dom, w["dim"], n) * nelem
+        flops = sum(algorithmic_flops_per_element(dom, w["dim"], N + 1) * E ** w["dim"] for E, N in shapes)
         achieved = flops / avg_s / 1e12
         peak = PEAK_FP32_TFLOPS if fp32 else PEAK_FP64_TFLOPS
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "kernel": "%s%d_kernel<%s,%d>" % (names[dom], w["dim"], "float" if fp32 else "double", n)}
+                "kernel": kname or "%s%d_kernel<%s,%d>" % (names[dom], w["dim"], "float" if fp32 else "double",
+                                                         w["N"] + 1)}
     key = "%s@%s@%s" % (roof["kernel"], args.workload, args.precision)
     tr = TRAFFIC.get(key)
     roof["traffic"] = tr["bytes"] if tr and tr["src"] == kernel_src_hash() else None
@@ -295,10 +325,12 @@ def gpu_arm(args, world, rank, local):
     roof["timing"] = "CUDA events around 1 in %d launches of each kernel kind, on the launching stream, " \
                      "inside the timed region" % args.profile_every
 
-    out = {"metric": METRIC, "value": value, "unit": "gradient evals/s", "n_gpus": world, "steps": args.steps,
+    unit = "instance gradient evals/s" if args.workload == "batch" else "gradient evals/s"
+    out = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": w["data"],
            "config": {"workload": w["desc"], "dim": w["dim"], "E": w["E"], "N": w["N"], "unknowns": s.ndof,
+                      "instances": units,
                       "scheme": scheme, "dt": dt, "rk_steps": nsteps, "trajectory": w["ckpt"],
                       "precision": args.precision, "parallelism": "replicas" if world > 1 else "single GPU",
                       "l2": "inputs larger than L2: every step writes and re-reads the stored stage trajectory "
@@ -314,7 +346,7 @@ def gpu_arm(args, world, rank, local):
         for _ in range(args.steps):
             Jh, gh = s.objective_grad(u0_h, uo_h, dt, nsteps, scheme, host=True)
         t1 = time.perf_counter()
-        out["e2e"] = {"value": args.steps / (t1 - t0), "unit": "gradient evals/s",
+        out["e2e"] = {"value": args.steps * units / (t1 - t0), "unit": unit,
                       "h2d_bytes_per_step": 2 * s.ndof * 8, "d2h_bytes_per_step": s.ndof * 8 + 8}
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)

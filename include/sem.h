@@ -137,6 +137,17 @@ int sem_objective_grad(sem_t h, int scheme, double dt, int nsteps,
                        const double* u0, const double* u_obs,
                        double* J_host, double* grad, void* stream);
 
+/* CUDA-graph execution of sem_objective_grad (and sem_batch_objective_grad):
+ * with enable != 0 the first call records the whole launch sequence of the
+ * gradient evaluation (forward sweep with trajectory storage, misfit, terminal
+ * adjoint, backward sweep) into a CUDA graph on a private stream, after making
+ * every allocation it needs, and each later call with the same scheme, dt,
+ * nsteps and u0 / u_obs / grad pointers replays that graph on `stream`.  A
+ * call with other arguments records a new graph.  Opt-in kernel timing is
+ * suspended while recording.  enable = 0 releases the graph. */
+int sem_set_graph(sem_t h, int enable);
+long long sem_graph_replays(sem_t h);   /* graph launches so far; -1 for a null handle */
+
 /* Host-only: optimal number of extra forward steps (advances) the binomial
  * schedule spends to reverse `nsteps` steps from a stored start state with
  * `slots` further state slots (Sec. 5.3, revolve).  Returns SEM_ERR_ARG for
@@ -159,6 +170,40 @@ int sem_sweep_stats(sem_t h, long long* out3);
  * two event records; the stream waits once per 4096 timed launches. */
 int sem_profile(sem_t h, int every);
 int sem_profile_read(sem_t h, double* ms4, long long* count4, int reset);
+
+/* ---------------------------------------------------------------- batches
+ * Many independent optimisation problems of uneven size (the paper solves one;
+ * this serves ensembles of them).  sem_batch_create makes one handle for
+ * `count` independent periodic 2D viscous-Burgers instances on [0, L)^2,
+ * instance k with E[k] elements per direction of order N[k] in {3, 5, 7, 9}
+ * and viscosity nu[k] >= 0.  `common` (may be NULL) supplies L and the
+ * checkpoint mode, slots and budget; precision must be SEM_PREC_FP64.
+ * The handle works with every state entry point (sem_rhs, sem_jac_apply,
+ * sem_jacT_apply, sem_rk_forward, sem_rk_adjoint, sem_objective,
+ * sem_objective_grad) on PACKED vectors: instance k occupies
+ * [offset, offset + ndof) of sem_batch_layout, in the single-instance layout.
+ * All instances advance with the same scheme and dt; each operator pass is one
+ * persistent launch over all instances' elements plus one gather-scatter
+ * launch, and every instance's result is bitwise equal to its own handle's.
+ * The misfit of sem_objective / sem_objective_grad is the sum over instances.
+ * Host-only; SEM_ERR_ARG for count < 1, null arrays or an unsupported instance. */
+int sem_batch_create(int count, const int* E, const int* N, const double* nu,
+                     const sem_opts* common, sem_t* out);
+int sem_batch_count(sem_t h);   /* 0 for a single-instance handle */
+int sem_batch_layout(sem_t h, int k, size_t* offset, size_t* ndof);
+int sem_batch_coords(sem_t h, int k, double* x_host);   /* instance k's G node coordinates */
+
+/* Autotuner of the batched element kernel: times the J^T element pass with
+ * 64, 128, 192 and 256 threads per block (elements per block = threads / (N+1)
+ * per instance) and keeps the fastest; ms4 (may be NULL) receives the four
+ * times, *threads the choice.  The first operator apply on a batch runs it
+ * when it has not run yet; both synchronise `stream`. */
+int sem_batch_autotune(sem_t h, double* ms4, int* threads, void* stream);
+
+/* sem_objective_grad for a batch with the per-instance misfits J_host[count]. */
+int sem_batch_objective_grad(sem_t h, int scheme, double dt, int nsteps,
+                             const double* u0, const double* u_obs,
+                             double* J_host, double* grad, void* stream);
 
 /* Size of the fixed device array used by sem_rhs_noalloc (16 MiB). */
 #define SEM_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)

@@ -57,6 +57,15 @@ _SIGS = {
     "sem_profile": (_I, [_H, _I]),
     "sem_profile_read": (_I, [_H, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), _I]),
     "sem_rhs_noalloc": (_I, [_H, _P, _P, _P]),
+    "sem_set_graph": (_I, [_H, _I]),
+    "sem_graph_replays": (ctypes.c_longlong, [_H]),
+    "sem_batch_create": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D),
+                              ctypes.POINTER(sem_opts), ctypes.POINTER(_H)]),
+    "sem_batch_count": (_I, [_H]),
+    "sem_batch_layout": (_I, [_H, _I, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+    "sem_batch_coords": (_I, [_H, _I, _P]),
+    "sem_batch_autotune": (_I, [_H, ctypes.POINTER(_D), ctypes.POINTER(_I), _P]),
+    "sem_batch_objective_grad": (_I, [_H, _I, _D, _I, _P, _P, ctypes.POINTER(_D), _P, _P]),
     "sem_last_error": (ctypes.c_char_p, []),
 }
 

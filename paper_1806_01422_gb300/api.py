@@ -128,6 +128,13 @@ class Sem:
                                            _stream(self.device)))
         return J.value, (grad.cpu() if host else grad)
 
+    def use_graph(self, enable=True):
+        """Record the gradient evaluation as a CUDA graph once and replay it (sem_set_graph)."""
+        L.check(L.lib().sem_set_graph(self._h, 1 if enable else 0))
+
+    def graph_replays(self):
+        return int(L.lib().sem_graph_replays(self._h))
+
     def profile(self, every=1):
         """Time one launch in `every` per kernel kind (0: off)."""
         L.check(L.lib().sem_profile(self._h, int(every)))
@@ -143,6 +150,67 @@ class Sem:
         out = (ctypes.c_longlong * 3)()
         L.check(L.lib().sem_sweep_stats(self._h, out))
         return {"forward_rhs": out[0], "adjoint_rhs": out[1], "adjoint_jacT": out[2]}
+
+
+class SemBatch(Sem):
+    """Independent 2D instances (E[k], N[k], nu[k]) on packed vectors (sem_batch_create).
+
+    Every Sem operation works on packed tensors of `ndof` values; `pack` and
+    `unpack` convert between per-instance (2, G_k, G_k) arrays and the packed form.
+    """
+
+    def __init__(self, E, N, nu, L_box=None, ckpt="auto", ckpt_slots=0, ckpt_budget_bytes=0, device=None):
+        count = len(E)
+        o = L.sem_opts(dim=2, E=0, N=0, nu=0.0, L=float(L_box or 0.0), precision=L.SEM_PREC_FP64,
+                       ckpt_mode=CKPT[ckpt], ckpt_slots=ckpt_slots, ckpt_budget_bytes=ckpt_budget_bytes)
+        Ea = (ctypes.c_int * count)(*[int(e) for e in E])
+        Na = (ctypes.c_int * count)(*[int(n) for n in N])
+        nua = (ctypes.c_double * count)(*[float(v) for v in nu])
+        h = ctypes.c_void_p()
+        L.check(L.lib().sem_batch_create(count, Ea, Na, nua, ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self.dim, self.count = 2, count
+        self.E, self.N, self.nu = list(E), list(N), list(nu)
+        self.ndof = int(L.lib().sem_ndof(h))
+        self.shape = (self.ndof,)
+        self.layout = []
+        for k in range(count):
+            off, n = ctypes.c_size_t(), ctypes.c_size_t()
+            L.check(L.lib().sem_batch_layout(h, k, ctypes.byref(off), ctypes.byref(n)))
+            self.layout.append((off.value, n.value))
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device()) \
+            if torch.cuda.is_available() else torch.device("cpu")
+
+    def coords(self, k):
+        x = np.empty(self.E[k] * self.N[k])
+        L.check(L.lib().sem_batch_coords(self._h, int(k), x.ctypes.data_as(ctypes.c_void_p)))
+        return x
+
+    def pack(self, fields):
+        """Concatenate per-instance (2, G_k, G_k) arrays into one packed float64 array."""
+        return np.concatenate([np.ascontiguousarray(f, dtype=np.float64).ravel() for f in fields])
+
+    def unpack(self, packed):
+        out = []
+        for k, (off, n) in enumerate(self.layout):
+            G = self.E[k] * self.N[k]
+            out.append(packed[off:off + n].reshape(2, G, G))
+        return out
+
+    def autotune(self):
+        ms = (ctypes.c_double * 4)()
+        th = ctypes.c_int()
+        L.check(L.lib().sem_batch_autotune(self._h, ms, ctypes.byref(th), _stream(self.device)))
+        return th.value, list(ms)
+
+    def objective_grad_each(self, u0, u_obs, dt, nsteps, scheme="rk4", grad=None):
+        """(per-instance misfits, packed gradient)."""
+        u0, u_obs = self._dev(u0, "u0"), self._dev(u_obs, "u_obs")
+        grad = self.empty() if grad is None else grad
+        J = (ctypes.c_double * self.count)()
+        L.check(L.lib().sem_batch_objective_grad(self._h, SCHEMES[scheme], float(dt), int(nsteps), self._p(u0),
+                                                 self._p(u_obs), J, self._p(grad), _stream(self.device)))
+        return list(J), grad
 
 
 def ckpt_plan(nsteps, slots):

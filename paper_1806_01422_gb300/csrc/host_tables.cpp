@@ -91,24 +91,40 @@ void derivative(const std::vector<double>& x, std::vector<double>& D) {
 }
 
 // Element-kernel matrices (row-major n x n, in this order):
-//   Dg = (2/h) Dhat,  Dv = -nu (2/h) W^-1 Dhat^T W,  Vz = nu (2/h) W Dhat W^-1,  Dd = -(2/h) Dhat^T.
+//   Dg  = (2/h) Dhat                                  (centro-antisymmetric)
+//   Sv  = -nu (2/h)^2 W^-1 Dhat^T W Dhat              (centro-symmetric)
+//   Svt = -nu (2/h)^2 Dhat^T W Dhat W^-1 = Sv^T       (centro-symmetric)
+//   Dd  = -(2/h) Dhat^T                               (centro-antisymmetric)
+// The symmetric pair is symmetrised exactly: A[i][j] = A[n-1-i][n-1-j].
 void kernel_matrices(const std::vector<double>& w, const std::vector<double>& Dh, double h, double nu,
                      std::vector<double>& mats) {
     const int n = (int)w.size();
     const double s = 2.0 / h;
     mats.assign((size_t)4 * n * n, 0.0);
     double* Dg = mats.data();
-    double* Dv = Dg + n * n;
-    double* Vz = Dv + n * n;
-    double* Dd = Vz + n * n;
+    double* Sv = Dg + n * n;
+    double* Svt = Sv + n * n;
+    double* Dd = Svt + n * n;
+    std::vector<double> K((size_t)n * n, 0.0);  // Dhat^T W Dhat
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) {
-            const double dij = Dh[(size_t)i * n + j], dji = Dh[(size_t)j * n + i];
-            Dg[i * n + j] = s * dij;
-            Dv[i * n + j] = -nu * s * dji * w[j] / w[i];
-            Vz[i * n + j] = nu * s * w[i] * dij / w[j];
-            Dd[i * n + j] = -s * dji;
+            double acc = 0.0;
+            for (int k = 0; k < n; ++k) acc += Dh[(size_t)k * n + i] * w[k] * Dh[(size_t)k * n + j];
+            K[(size_t)i * n + j] = acc;
         }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            Dg[i * n + j] = s * Dh[(size_t)i * n + j];
+            Sv[i * n + j] = -nu * s * s * K[(size_t)i * n + j] / w[i];
+            Svt[i * n + j] = -nu * s * s * K[(size_t)i * n + j] / w[j];
+            Dd[i * n + j] = -s * Dh[(size_t)j * n + i];
+        }
+    for (double* A : {Sv, Svt}) {
+        std::vector<double> S(A, A + n * n);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j)
+                A[i * n + j] = 0.5 * (S[(size_t)i * n + j] + S[(size_t)(n - 1 - i) * n + (n - 1 - j)]);
+    }
 }
 
 }  // namespace semh

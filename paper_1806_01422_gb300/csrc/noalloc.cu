@@ -96,6 +96,8 @@ extern "C" int sem_rhs_noalloc(sem_t h, const double* u, double* f, void* stream
     a.N = v.N;
     a.G = v.G;
     a.nelem = v.nelem;
+    a.plane = (unsigned)v.ndof;
+    a.in_f2 = 0;
     cudaError_t e;
     if (v.dim == 1) e = v.fp32 ? semk::launch_elem<float, 1>(v.np, semk::OP_RHS, v.mats, a, s) : semk::launch_elem<double, 1>(v.np, semk::OP_RHS, v.mats, a, s);
     else if (v.dim == 2) e = v.fp32 ? semk::launch_elem<float, 2>(v.np, semk::OP_RHS, v.mats, a, s) : semk::launch_elem<double, 2>(v.np, semk::OP_RHS, v.mats, a, s);

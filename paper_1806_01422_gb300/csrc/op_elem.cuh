@@ -6,10 +6,12 @@
 // kernel, which also applies the Runge-Kutta epilogue.
 //
 // Local results (see op_kernels.cuh for the matrices):
-//   F :  f_c   = sum_j Dv_j Dg_j U_c - sum_j U_j Dg_j U_c
-//   J :  f_c   = sum_j Dv_j Dg_j W_c - sum_j (W_j Dg_j U_c + U_j Dg_j W_c)
-//   JT:  f_l   = sum_j Dd_j (Vz_j Z_l + U_j Z_l) - sum_c Z_c Dg_l U_c,  Z = v / k
-// with Dg_j, Dv_j, Vz_j, Dd_j the 1D matrices applied along direction x_j.
+//   F :  f_c   = sum_j [ Sv_j U_c - U_j Dg_j U_c ]
+//   J :  f_c   = sum_j [ Sv_j W_c - (W_j Dg_j U_c + U_j Dg_j W_c) ]
+//   JT:  f_l   = sum_j [ Svt_j Z_l + Dd_j (U_j Z_l) ] - sum_c Z_c Dg_l U_c,   Z = v / k
+// with Dg_j, Sv_j, Svt_j, Dd_j the 1D matrices applied along direction x_j.  Each
+// bracket is one pass along direction j; in 3D the x and y passes write two
+// partial-result tiles and the z pass adds them and writes the result.
 #pragma once
 #include "op_kernels.cuh"
 
@@ -17,16 +19,20 @@ namespace semk {
 
 template <int D>
 __host__ __device__ constexpr int tiles_per_elem(int op) {
-    // F: U[d] + G (d-1) + F ; J: U[d] + W[d] + G (d-1) + F + A ; JT: U[d] + Z[d] + G (d-1) + F
-    return op == OP_RHS ? (2 * D) : (op == OP_JAC ? (3 * D + 1) : (3 * D));
+    // inputs (U; U and W; U and Z) plus the partial results (F; F and A in 3D)
+    return (op == OP_RHS ? D : 2 * D) + (D == 3 ? 2 : 1);
 }
 
 // ------------------------------------------------------------------ loaders
-// In the FP32 form each element tile of U (and W) holds U - U_ref, with U_ref
-// the value at the element's first node, formed in FP64 before rounding to
-// FP32.  The 1D matrices annihilate constants (Dhat 1 = 0), so gradients see
-// only the small in-element variation and lose far less to FP32 cancellation;
-// pointwise products add U_ref back.  The FP64 form stores U itself (ref = 0).
+// FP64 form: tiles hold the input doubles.
+// FP32 form: every input node is read as a float pair (hi, lo) -- either from the
+// two FP32 planes of a sweep-internal state, or split from a caller's double
+// with integer instructions (split_bits), which give the same pair -- and a tile
+// of U (or W) holds U - U_ref formed as (hi - hi_ref) + (lo - lo_ref) in FP32,
+// U_ref being the value at the element's first node.  The 1D matrices applied
+// to U and W annihilate constants (Dhat 1 = 0), so gradients and viscous terms
+// see only the small in-element variation and lose little to FP32
+// cancellation; pointwise products add hi_ref back.  Z = v / k keeps hi only.
 template <typename T>
 struct RefSub {
     static constexpr bool on = sizeof(T) == 4;
@@ -38,67 +44,82 @@ __device__ __forceinline__ T with_ref(T ref, T x) {
     else return x;
 }
 
+__device__ __forceinline__ void read_pair(const ElemArgs& a, const void* g, size_t i, float& hi, float& lo) {
+    if (a.in_f2) {
+        hi = __ldg((const float*)g + i);
+        lo = __ldg((const float*)g + a.plane + i);
+    } else {
+        split_bits(__ldg((const double*)g + i), hi, lo);
+    }
+}
+
+// 1/k for k = 2^nb sharing elements (exact)
+template <typename T>
+__device__ __forceinline__ T inv_mult(int nb) {
+    return nb == 0 ? (T)1 : (nb == 1 ? (T)0.5 : (nb == 2 ? (T)0.25 : (T)0.125));
+}
+
+// Value stored in a tile for global node i: the input (FP64), U - U_ref (FP32), or
+// v / k when scale_mult (nb = boundary count of the node, k = 2^nb).
+template <typename T>
+__device__ __forceinline__ T tile_value(const ElemArgs& a, const void* g, size_t i, bool scale_mult, int nb,
+                                        float ref_hi, float ref_lo) {
+    if constexpr (sizeof(T) == 8) {
+        const double x = __ldg((const double*)g + i);
+        return scale_mult ? x * inv_mult<double>(nb) : x;
+    } else {
+        float hi, lo;
+        read_pair(a, g, i, hi, lo);
+        if (scale_mult) return hi * inv_mult<float>(nb);
+        return __fadd_rn(__fsub_rn(hi, ref_hi), __fsub_rn(lo, ref_lo));
+    }
+}
+
 // Load component c of a global field into an element tile (d = 3): thread t of
 // the element owns column (i, j) = (t % n, t / n) and walks k.  `scale_mult`
 // multiplies each node by 1/k (k = elements sharing it), used for Z = v / k.
-// Returns the reference value subtracted from the tile (0 unless FP32 and not Z).
+// Returns the reference value of the tile (0 unless FP32 and not Z).
 template <typename T, int NP>
-__device__ __forceinline__ T load3(T* tile, const double* __restrict__ g, int c, int ex, int ey,
-                                   int ez, int t, bool valid, const ElemArgs& a, bool scale_mult) {
+__device__ __forceinline__ T load3(T* tile, const void* g, int c, int ex, int ey, int ez, int t, bool valid,
+                                   const ElemArgs& a, bool scale_mult) {
     using Tl = Tile<NP>;
     const int i = t % NP, j = t / NP;
     const int N = a.N, G = a.G;
     const int gx = wrap(ex * N + i, G), gy = wrap(ey * N + j, G);
-    const bool bij = (i == 0 || i == N), bj = (j == 0 || j == N);
-    const T sij = scale_mult ? (T)((bij ? 0.5 : 1.0) * (bj ? 0.5 : 1.0)) : (T)1;
-    double ref = 0.0;
-    if (RefSub<T>::on && !scale_mult && valid) ref = __ldg(g + gidx3(c, ez * N, ey * N, ex * N, G));
+    const int nbij = (int)(i == 0 || i == N) + (int)(j == 0 || j == N);
+    float ref_hi = 0.f, ref_lo = 0.f;
+    if (RefSub<T>::on && !scale_mult && valid) read_pair(a, g, gidx3(c, ez * N, ey * N, ex * N, G), ref_hi, ref_lo);
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
         const int gz = wrap(ez * N + k, G);
         T v = (T)0;
-        if (valid) {
-            const double x = __ldg(g + gidx3(c, gz, gy, gx, G));
-            if (RefSub<T>::on && !scale_mult) {
-                v = (T)(x - ref);
-            } else {
-                v = (T)x;
-                if (scale_mult) v = v * sij * ((k == 0 || k == N) ? (T)0.5 : (T)1);
-            }
-        }
+        if (valid) v = tile_value<T>(a, g, gidx3(c, gz, gy, gx, G), scale_mult,
+                                     nbij + (int)(k == 0 || k == N), ref_hi, ref_lo);
         tile[(k * NP + j) * Tl::P + i] = v;
     }
-    return (T)ref;
+    return (T)ref_hi;
 }
 
 // d = 2: thread t owns row j = t and walks i.
 template <typename T, int NP>
-__device__ __forceinline__ T load2(T* tile, const double* __restrict__ g, int c, int ex, int ey,
-                                   int t, bool valid, const ElemArgs& a, bool scale_mult) {
+__device__ __forceinline__ T load2(T* tile, const void* g, int c, int ex, int ey, int t, bool valid,
+                                   const ElemArgs& a, bool scale_mult) {
     using Tl = Tile<NP>;
     const int j = t;
     const int N = a.N, G = a.G;
     const int gy = wrap(ey * N + j, G);
-    const T sj = (scale_mult && (j == 0 || j == N)) ? (T)0.5 : (T)1;
+    const int nbj = (int)(j == 0 || j == N);
     const size_t row = ((size_t)c * G + gy) * G;
-    double ref = 0.0;
-    if (RefSub<T>::on && !scale_mult && valid) ref = __ldg(g + ((size_t)c * G + ey * N) * G + ex * N);
+    float ref_hi = 0.f, ref_lo = 0.f;
+    if (RefSub<T>::on && !scale_mult && valid) read_pair(a, g, ((size_t)c * G + ey * N) * G + ex * N, ref_hi, ref_lo);
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
         const int gx = wrap(ex * N + i, G);
         T v = (T)0;
-        if (valid) {
-            const double x = __ldg(g + row + gx);
-            if (RefSub<T>::on && !scale_mult) {
-                v = (T)(x - ref);
-            } else {
-                v = (T)x;
-                if (scale_mult) v = v * sj * ((i == 0 || i == N) ? (T)0.5 : (T)1);
-            }
-        }
+        if (valid) v = tile_value<T>(a, g, row + gx, scale_mult, nbj + (int)(i == 0 || i == N), ref_hi, ref_lo);
         tile[j * Tl::P + i] = v;
     }
-    return (T)ref;
+    return (T)ref_hi;
 }
 
 // ================================================================== d = 3
@@ -106,6 +127,66 @@ __device__ __forceinline__ T load2(T* tile, const double* __restrict__ g, int c,
 //   x-line (j, k) = (t % n, t / n): base t*P,                stride 1
 //   y-line (i, k) = (t % n, t / n): base (t/n)*S2 + t % n,   stride P
 //   z-line (i, j) = (t % n, t / n): base (t/n)*P + t % n,    stride S2
+// The z pass writes node (i, j, m) of the element-local result at m*n^2 + j*n + i,
+// so a warp stores contiguous runs.
+
+// One F pass along a direction: r = Sv x - Ud * (Dg x), x the line of U_c - ref.
+template <typename T, int NP, int STRIDE>
+__device__ __forceinline__ void rhs_pass(const OpMats<T, NP>& M, const T* sUc, const T* sUd, T rd, int base,
+                                         T (&r)[NP]) {
+    T x[NP], g[NP];
+    ld_line<T, NP, STRIDE>(sUc, base, x);
+    Pre<T, NP> p;
+    pre_add<T, NP>(x, p);
+    eo_apply<false, T, NP>(M.Dg, p, g);
+    eo_apply<true, T, NP>(M.Sv, p, r);
+#pragma unroll
+    for (int m = 0; m < NP; ++m) r[m] = fma(-with_ref(rd, sUd[base + m * STRIDE]), g[m], r[m]);
+}
+
+// One J pass: r = Sv W_c - (W_d Dg U_c + U_d Dg W_c).
+template <typename T, int NP, int STRIDE>
+__device__ __forceinline__ void jac_pass(const OpMats<T, NP>& M, const T* sUc, const T* sWc, const T* sUd,
+                                         const T* sWd, T ru, T rw, int base, T (&r)[NP]) {
+    T x[NP], gw[NP], gu[NP];
+    ld_line<T, NP, STRIDE>(sWc, base, x);
+    Pre<T, NP> p;
+    pre_add<T, NP>(x, p);
+    eo_apply<false, T, NP>(M.Dg, p, gw);
+    eo_apply<true, T, NP>(M.Sv, p, r);
+    ld_line<T, NP, STRIDE>(sUc, base, x);
+    eo_apply<false, T, NP>(M.Dg, x, gu);
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+        const int id = base + m * STRIDE;
+        r[m] -= fma(with_ref(rw, sWd[id]), gu[m], with_ref(ru, sUd[id]) * gw[m]);
+    }
+}
+
+// One J^T pass: r = Svt Z_l + Dd (U_d Z_l), plus -sum_c Z_c Dg U_c when d == l.
+template <typename T, int NP, int STRIDE, int D>
+__device__ __forceinline__ void jact_pass(const OpMats<T, NP>& M, T* const* sU, T* const* sZ, const T* rU,
+                                          int l, int d, int base, T (&r)[NP]) {
+    T z[NP], q[NP], dv[NP];
+    ld_line<T, NP, STRIDE>(sZ[l], base, z);
+    eo_apply<true, T, NP>(M.Svt, z, r);
+#pragma unroll
+    for (int m = 0; m < NP; ++m) q[m] = with_ref(rU[d], sU[d][base + m * STRIDE]) * z[m];
+    eo_apply<false, T, NP>(M.Dd, q, dv);
+#pragma unroll
+    for (int m = 0; m < NP; ++m) r[m] += dv[m];
+    if (l == d) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            T x[NP], g[NP];
+            ld_line<T, NP, STRIDE>(sU[c], base, x);
+            eo_apply<false, T, NP>(M.Dg, x, g);
+#pragma unroll
+            for (int m = 0; m < NP; ++m) r[m] = fma(-sZ[c][base + m * STRIDE], g[m], r[m]);
+        }
+    }
+}
+
 template <typename T, int NP>
 __global__ void rhs3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
     using Tl = Tile<NP>;
@@ -116,63 +197,27 @@ __global__ void rhs3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
     const bool valid = e < a.nelem;
     T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)el * tiles_per_elem<3>(OP_RHS) * S3;
     T* sU[3] = {sm, sm + S3, sm + 2 * S3};
-    T* sG0 = sm + 3 * S3;
-    T* sG1 = sm + 4 * S3;
-    T* sF = sm + 5 * S3;
+    T* sF = sm + 3 * S3;
+    T* sA = sm + 4 * S3;
     const int ex = e % a.E, ey = (e / a.E) % a.E, ez = e / (a.E * a.E);
     T rU[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) rU[c] = load3<T, NP>(sU[c], a.u, c, ex, ey, ez, t, valid, a, false);
     __syncthreads();
     const int xb = t * P, yb = (t / NP) * S2 + t % NP, zb = (t / NP) * P + t % NP;
-    T* out = reinterpret_cast<T*>(a.lvec) + (size_t)e * 3 * (NP * NP * NP);
+    T* out = reinterpret_cast<T*>(a.lvec) + (size_t)e * 3 * (NP * NP * NP) + (t / NP) * NP + t % NP;
 #pragma unroll 1
     for (int c = 0; c < 3; ++c) {
-        const T* sUc = sU[c];
-        {   // x and y gradients of U_c
-            T x[NP], g[NP];
-            ld_line<T, NP, 1>(sUc, xb, x);
-            eo_apply<T, NP>(M.Dg, x, g);
-            st_line<T, NP, 1>(sG0, xb, g);
-            ld_line<T, NP, P>(sUc, yb, x);
-            eo_apply<T, NP>(M.Dg, x, g);
-            st_line<T, NP, P>(sG1, yb, g);
-        }
+        T r[NP];
+        rhs_pass<T, NP, 1>(M, sU[c], sU[0], rU[0], xb, r);
+        st_line<T, NP, 1>(sF, xb, r);
+        rhs_pass<T, NP, P>(M, sU[c], sU[1], rU[1], yb, r);
+        st_line<T, NP, P>(sA, yb, r);
         __syncthreads();
-        {   // z gradient, advection, z part of the viscous divergence
-            T x[NP], gz[NP], f[NP];
-            ld_line<T, NP, S2>(sUc, zb, x);
-            eo_apply<T, NP>(M.Dg, x, gz);
-            eo_apply<T, NP>(M.Dv, gz, f);
+        rhs_pass<T, NP, S2>(M, sU[c], sU[2], rU[2], zb, r);
+        if (valid) {
 #pragma unroll
-            for (int m = 0; m < NP; ++m) {
-                const int id = zb + m * S2;
-                T adv = with_ref(rU[0], sU[0][id]) * sG0[id];
-                adv = fma(with_ref(rU[1], sU[1][id]), sG1[id], adv);
-                adv = fma(with_ref(rU[2], sU[2][id]), gz[m], adv);
-                f[m] -= adv;
-            }
-            st_line<T, NP, S2>(sF, zb, f);
-        }
-        __syncthreads();
-        {   // x part of the viscous divergence
-            T g[NP], f[NP];
-            ld_line<T, NP, 1>(sG0, xb, g);
-            ld_line<T, NP, 1>(sF, xb, f);
-            eo_apply_add<T, NP>(M.Dv, g, f);
-            st_line<T, NP, 1>(sF, xb, f);
-        }
-        __syncthreads();
-        {   // y part, then the element-local result
-            T g[NP], f[NP];
-            ld_line<T, NP, P>(sG1, yb, g);
-            ld_line<T, NP, P>(sF, yb, f);
-            eo_apply_add<T, NP>(M.Dv, g, f);
-            if (valid) {
-                T* o = out + (size_t)c * (NP * NP * NP) + (t / NP) * NP * NP + t % NP;
-#pragma unroll
-                for (int m = 0; m < NP; ++m) o[m * NP] = f[m];
-            }
+            for (int m = 0; m < NP; ++m) out[(size_t)c * NP * NP * NP + m * NP * NP] = r[m] + (sF[zb + m * S2] + sA[zb + m * S2]);
         }
         __syncthreads();
     }
@@ -189,10 +234,8 @@ __global__ void jac3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
     T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)el * tiles_per_elem<3>(OP_JAC) * S3;
     T* sU[3] = {sm, sm + S3, sm + 2 * S3};
     T* sW[3] = {sm + 3 * S3, sm + 4 * S3, sm + 5 * S3};
-    T* sG0 = sm + 6 * S3;
-    T* sG1 = sm + 7 * S3;
-    T* sF = sm + 8 * S3;
-    T* sA = sm + 9 * S3;
+    T* sF = sm + 6 * S3;
+    T* sA = sm + 7 * S3;
     const int ex = e % a.E, ey = (e / a.E) % a.E, ez = e / (a.E * a.E);
     T rU[3], rW[3];
 #pragma unroll
@@ -202,69 +245,19 @@ __global__ void jac3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
     }
     __syncthreads();
     const int xb = t * P, yb = (t / NP) * S2 + t % NP, zb = (t / NP) * P + t % NP;
-    T* out = reinterpret_cast<T*>(a.lvec) + (size_t)e * 3 * (NP * NP * NP);
+    T* out = reinterpret_cast<T*>(a.lvec) + (size_t)e * 3 * (NP * NP * NP) + (t / NP) * NP + t % NP;
 #pragma unroll 1
     for (int c = 0; c < 3; ++c) {
-        {
-            T x[NP], gw[NP], gu[NP], f[NP];
-            // x: gradient of W_c to sG0, advection x-term to sF
-            ld_line<T, NP, 1>(sW[c], xb, x);
-            eo_apply<T, NP>(M.Dg, x, gw);
-            st_line<T, NP, 1>(sG0, xb, gw);
-            ld_line<T, NP, 1>(sU[c], xb, x);
-            eo_apply<T, NP>(M.Dg, x, gu);
-#pragma unroll
-            for (int m = 0; m < NP; ++m)
-                f[m] = -fma(with_ref(rW[0], sW[0][xb + m]), gu[m], with_ref(rU[0], sU[0][xb + m]) * gw[m]);
-            st_line<T, NP, 1>(sF, xb, f);
-            // y: gradient of W_c to sG1, advection y-term to sA
-            ld_line<T, NP, P>(sW[c], yb, x);
-            eo_apply<T, NP>(M.Dg, x, gw);
-            st_line<T, NP, P>(sG1, yb, gw);
-            ld_line<T, NP, P>(sU[c], yb, x);
-            eo_apply<T, NP>(M.Dg, x, gu);
-#pragma unroll
-            for (int m = 0; m < NP; ++m) {
-                const int id = yb + m * P;
-                f[m] = -fma(with_ref(rW[1], sW[1][id]), gu[m], with_ref(rU[1], sU[1][id]) * gw[m]);
-            }
-            st_line<T, NP, P>(sA, yb, f);
-        }
+        T r[NP];
+        jac_pass<T, NP, 1>(M, sU[c], sW[c], sU[0], sW[0], rU[0], rW[0], xb, r);
+        st_line<T, NP, 1>(sF, xb, r);
+        jac_pass<T, NP, P>(M, sU[c], sW[c], sU[1], sW[1], rU[1], rW[1], yb, r);
+        st_line<T, NP, P>(sA, yb, r);
         __syncthreads();
-        {
-            T x[NP], gw[NP], gu[NP], f[NP];
-            ld_line<T, NP, S2>(sW[c], zb, x);
-            eo_apply<T, NP>(M.Dg, x, gw);
-            ld_line<T, NP, S2>(sU[c], zb, x);
-            eo_apply<T, NP>(M.Dg, x, gu);
-            eo_apply<T, NP>(M.Dv, gw, f);
+        jac_pass<T, NP, S2>(M, sU[c], sW[c], sU[2], sW[2], rU[2], rW[2], zb, r);
+        if (valid) {
 #pragma unroll
-            for (int m = 0; m < NP; ++m) {
-                const int id = zb + m * S2;
-                const T adv = fma(with_ref(rW[2], sW[2][id]), gu[m], with_ref(rU[2], sU[2][id]) * gw[m]);
-                f[m] = (f[m] - adv) + (sF[id] + sA[id]);
-            }
-            st_line<T, NP, S2>(sF, zb, f);
-        }
-        __syncthreads();
-        {
-            T g[NP], f[NP];
-            ld_line<T, NP, 1>(sG0, xb, g);
-            ld_line<T, NP, 1>(sF, xb, f);
-            eo_apply_add<T, NP>(M.Dv, g, f);
-            st_line<T, NP, 1>(sF, xb, f);
-        }
-        __syncthreads();
-        {
-            T g[NP], f[NP];
-            ld_line<T, NP, P>(sG1, yb, g);
-            ld_line<T, NP, P>(sF, yb, f);
-            eo_apply_add<T, NP>(M.Dv, g, f);
-            if (valid) {
-                T* o = out + (size_t)c * (NP * NP * NP) + (t / NP) * NP * NP + t % NP;
-#pragma unroll
-                for (int m = 0; m < NP; ++m) o[m * NP] = f[m];
-            }
+            for (int m = 0; m < NP; ++m) out[(size_t)c * NP * NP * NP + m * NP * NP] = r[m] + (sF[zb + m * S2] + sA[zb + m * S2]);
         }
         __syncthreads();
     }
@@ -281,9 +274,8 @@ __global__ void jact3_kernel(const __grid_constant__ OpMats<T, NP> M, const Elem
     T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)el * tiles_per_elem<3>(OP_JACT) * S3;
     T* sU[3] = {sm, sm + S3, sm + 2 * S3};
     T* sZ[3] = {sm + 3 * S3, sm + 4 * S3, sm + 5 * S3};
-    T* sG0 = sm + 6 * S3;
-    T* sG1 = sm + 7 * S3;
-    T* sF = sm + 8 * S3;
+    T* sF = sm + 6 * S3;
+    T* sA = sm + 7 * S3;
     const int ex = e % a.E, ey = (e / a.E) % a.E, ez = e / (a.E * a.E);
     T rU[3];
 #pragma unroll
@@ -293,97 +285,19 @@ __global__ void jact3_kernel(const __grid_constant__ OpMats<T, NP> M, const Elem
     }
     __syncthreads();
     const int xb = t * P, yb = (t / NP) * S2 + t % NP, zb = (t / NP) * P + t % NP;
-    T* out = reinterpret_cast<T*>(a.lvec) + (size_t)e * 3 * (NP * NP * NP);
+    T* out = reinterpret_cast<T*>(a.lvec) + (size_t)e * 3 * (NP * NP * NP) + (t / NP) * NP + t % NP;
 #pragma unroll 1
     for (int l = 0; l < 3; ++l) {
-        const T* sZl = sZ[l];
-        {
-            T z[NP], q[NP];
-            // x: flux q_x = Vz Z_l + U_x Z_l
-            ld_line<T, NP, 1>(sZl, xb, z);
-            eo_apply<T, NP>(M.Vz, z, q);
-#pragma unroll
-            for (int m = 0; m < NP; ++m) q[m] = fma(with_ref(rU[0], sU[0][xb + m]), z[m], q[m]);
-            st_line<T, NP, 1>(sG0, xb, q);
-            if (l == 0) {  // reaction term along x: -sum_c Z_c Dg_x U_c
-                T acc[NP], x[NP], g[NP];
-#pragma unroll
-                for (int m = 0; m < NP; ++m) acc[m] = (T)0;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    ld_line<T, NP, 1>(sU[c], xb, x);
-                    eo_apply<T, NP>(M.Dg, x, g);
-#pragma unroll
-                    for (int m = 0; m < NP; ++m) acc[m] = fma(sZ[c][xb + m], g[m], acc[m]);
-                }
-#pragma unroll
-                for (int m = 0; m < NP; ++m) acc[m] = -acc[m];
-                st_line<T, NP, 1>(sF, xb, acc);
-            }
-            // y: flux q_y
-            ld_line<T, NP, P>(sZl, yb, z);
-            eo_apply<T, NP>(M.Vz, z, q);
-#pragma unroll
-            for (int m = 0; m < NP; ++m) q[m] = fma(with_ref(rU[1], sU[1][yb + m * P]), z[m], q[m]);
-            st_line<T, NP, P>(sG1, yb, q);
-            if (l == 1) {
-                T acc[NP], x[NP], g[NP];
-#pragma unroll
-                for (int m = 0; m < NP; ++m) acc[m] = (T)0;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    ld_line<T, NP, P>(sU[c], yb, x);
-                    eo_apply<T, NP>(M.Dg, x, g);
-#pragma unroll
-                    for (int m = 0; m < NP; ++m) acc[m] = fma(sZ[c][yb + m * P], g[m], acc[m]);
-                }
-#pragma unroll
-                for (int m = 0; m < NP; ++m) acc[m] = -acc[m];
-                st_line<T, NP, P>(sF, yb, acc);
-            }
-        }
+        T r[NP];
+        jact_pass<T, NP, 1, 3>(M, sU, sZ, rU, l, 0, xb, r);
+        st_line<T, NP, 1>(sF, xb, r);
+        jact_pass<T, NP, P, 3>(M, sU, sZ, rU, l, 1, yb, r);
+        st_line<T, NP, P>(sA, yb, r);
         __syncthreads();
-        {   // z: flux, its divergence, and the z reaction term (l == 2)
-            T z[NP], q[NP], f[NP];
-            ld_line<T, NP, S2>(sZl, zb, z);
-            eo_apply<T, NP>(M.Vz, z, q);
+        jact_pass<T, NP, S2, 3>(M, sU, sZ, rU, l, 2, zb, r);
+        if (valid) {
 #pragma unroll
-            for (int m = 0; m < NP; ++m) q[m] = fma(with_ref(rU[2], sU[2][zb + m * S2]), z[m], q[m]);
-            eo_apply<T, NP>(M.Dd, q, f);
-            if (l == 2) {
-                T x[NP], g[NP];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    ld_line<T, NP, S2>(sU[c], zb, x);
-                    eo_apply<T, NP>(M.Dg, x, g);
-#pragma unroll
-                    for (int m = 0; m < NP; ++m) f[m] = fma(-sZ[c][zb + m * S2], g[m], f[m]);
-                }
-            } else {
-#pragma unroll
-                for (int m = 0; m < NP; ++m) f[m] += sF[zb + m * S2];
-            }
-            st_line<T, NP, S2>(sF, zb, f);
-        }
-        __syncthreads();
-        {
-            T q[NP], f[NP];
-            ld_line<T, NP, 1>(sG0, xb, q);
-            ld_line<T, NP, 1>(sF, xb, f);
-            eo_apply_add<T, NP>(M.Dd, q, f);
-            st_line<T, NP, 1>(sF, xb, f);
-        }
-        __syncthreads();
-        {
-            T q[NP], f[NP];
-            ld_line<T, NP, P>(sG1, yb, q);
-            ld_line<T, NP, P>(sF, yb, f);
-            eo_apply_add<T, NP>(M.Dd, q, f);
-            if (valid) {
-                T* o = out + (size_t)l * (NP * NP * NP) + (t / NP) * NP * NP + t % NP;
-#pragma unroll
-                for (int m = 0; m < NP; ++m) o[m * NP] = f[m];
-            }
+            for (int m = 0; m < NP; ++m) out[(size_t)l * NP * NP * NP + m * NP * NP] = r[m] + (sF[zb + m * S2] + sA[zb + m * S2]);
         }
         __syncthreads();
     }
@@ -391,78 +305,57 @@ __global__ void jact3_kernel(const __grid_constant__ OpMats<T, NP> M, const Elem
 
 // ================================================================== d = 2
 // n threads per element.  x-line j = t: base t*P, stride 1; y-line i = t: base t,
-// stride P.  The last pass runs along y so that the element-local output of a
-// warp is written in contiguous rows.
+// stride P.  The x pass writes its part to a tile; the y pass adds it and writes
+// node (i, m) of the element-local result at m*n + i (contiguous over a warp).
+// Element e (thread t of the element, slot el of the block's shared memory) of a d = 2 F apply.
 template <typename T, int NP>
-__global__ void rhs2_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
+__device__ __forceinline__ void rhs2_body(const OpMats<T, NP>& M, const ElemArgs& a, int e, int t, int el,
+                                        bool valid, unsigned char* smem_raw) {
     using Tl = Tile<NP>;
-    constexpr int TPE = NP, P = Tl::P, S2 = Tl::S2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int el = threadIdx.x / TPE, t = threadIdx.x % TPE;
-    const int e = blockIdx.x * (blockDim.x / TPE) + el;
-    const bool valid = e < a.nelem;
+    constexpr int P = Tl::P, S2 = Tl::S2;
     T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)el * tiles_per_elem<2>(OP_RHS) * S2;
     T* sU[2] = {sm, sm + S2};
-    T* sG1 = sm + 2 * S2;
-    T* sF = sm + 3 * S2;
+    T* sF = sm + 2 * S2;
     const int ex = e % a.E, ey = e / a.E;
     T rU[2];
 #pragma unroll
     for (int c = 0; c < 2; ++c) rU[c] = load2<T, NP>(sU[c], a.u, c, ex, ey, t, valid, a, false);
     __syncthreads();
     const int xb = t * P, yb = t;
-    T* out = reinterpret_cast<T*>(a.lvec) + (size_t)e * 2 * (NP * NP);
+    T* out = reinterpret_cast<T*>(a.lvec) + (size_t)e * 2 * (NP * NP) + t;
 #pragma unroll 1
     for (int c = 0; c < 2; ++c) {
-        {
-            T x[NP], g[NP];
-            ld_line<T, NP, P>(sU[c], yb, x);
-            eo_apply<T, NP>(M.Dg, x, g);
-            st_line<T, NP, P>(sG1, yb, g);
-        }
+        T r[NP];
+        rhs_pass<T, NP, 1>(M, sU[c], sU[0], rU[0], xb, r);
+        st_line<T, NP, 1>(sF, xb, r);
         __syncthreads();
-        {
-            T x[NP], gx[NP], f[NP];
-            ld_line<T, NP, 1>(sU[c], xb, x);
-            eo_apply<T, NP>(M.Dg, x, gx);
-            eo_apply<T, NP>(M.Dv, gx, f);
+        rhs_pass<T, NP, P>(M, sU[c], sU[1], rU[1], yb, r);
+        if (valid) {
 #pragma unroll
-            for (int m = 0; m < NP; ++m) {
-                const int id = xb + m;
-                const T adv = fma(with_ref(rU[1], sU[1][id]), sG1[id], with_ref(rU[0], sU[0][id]) * gx[m]);
-                f[m] -= adv;
-            }
-            st_line<T, NP, 1>(sF, xb, f);
-        }
-        __syncthreads();
-        {
-            T g[NP], f[NP];
-            ld_line<T, NP, P>(sG1, yb, g);
-            ld_line<T, NP, P>(sF, yb, f);
-            eo_apply_add<T, NP>(M.Dv, g, f);
-            if (valid) {
-                T* o = out + (size_t)c * (NP * NP) + t;
-#pragma unroll
-                for (int m = 0; m < NP; ++m) o[m * NP] = f[m];
-            }
+            for (int m = 0; m < NP; ++m) out[(size_t)c * NP * NP + m * NP] = r[m] + sF[yb + m * P];
         }
         __syncthreads();
     }
 }
 
 template <typename T, int NP>
-__global__ void jac2_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
-    using Tl = Tile<NP>;
-    constexpr int TPE = NP, P = Tl::P, S2 = Tl::S2;
+__global__ void rhs2_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int el = threadIdx.x / TPE, t = threadIdx.x % TPE;
-    const int e = blockIdx.x * (blockDim.x / TPE) + el;
-    const bool valid = e < a.nelem;
+    const int el = threadIdx.x / NP, t = threadIdx.x % NP;
+    const int e = blockIdx.x * (blockDim.x / NP) + el;
+    rhs2_body<T, NP>(M, a, e, t, el, e < a.nelem, smem_raw);
+}
+
+// Element e (thread t of the element, slot el of the block's shared memory) of a d = 2 J apply.
+template <typename T, int NP>
+__device__ __forceinline__ void jac2_body(const OpMats<T, NP>& M, const ElemArgs& a, int e, int t, int el,
+                                        bool valid, unsigned char* smem_raw) {
+    using Tl = Tile<NP>;
+    constexpr int P = Tl::P, S2 = Tl::S2;
     T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)el * tiles_per_elem<2>(OP_JAC) * S2;
     T* sU[2] = {sm, sm + S2};
     T* sW[2] = {sm + 2 * S2, sm + 3 * S2};
-    T* sG1 = sm + 4 * S2;
-    T* sF = sm + 5 * S2;
+    T* sF = sm + 4 * S2;
     const int ex = e % a.E, ey = e / a.E;
     T rU[2], rW[2];
 #pragma unroll
@@ -472,68 +365,40 @@ __global__ void jac2_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
     }
     __syncthreads();
     const int xb = t * P, yb = t;
-    T* out = reinterpret_cast<T*>(a.lvec) + (size_t)e * 2 * (NP * NP);
+    T* out = reinterpret_cast<T*>(a.lvec) + (size_t)e * 2 * (NP * NP) + t;
 #pragma unroll 1
     for (int c = 0; c < 2; ++c) {
-        {
-            T x[NP], gw[NP], gu[NP], f[NP];
-            ld_line<T, NP, P>(sW[c], yb, x);
-            eo_apply<T, NP>(M.Dg, x, gw);
-            st_line<T, NP, P>(sG1, yb, gw);
-            ld_line<T, NP, P>(sU[c], yb, x);
-            eo_apply<T, NP>(M.Dg, x, gu);
-#pragma unroll
-            for (int m = 0; m < NP; ++m) {
-                const int id = yb + m * P;
-                f[m] = -fma(with_ref(rW[1], sW[1][id]), gu[m], with_ref(rU[1], sU[1][id]) * gw[m]);
-            }
-            st_line<T, NP, P>(sF, yb, f);
-        }
+        T r[NP];
+        jac_pass<T, NP, 1>(M, sU[c], sW[c], sU[0], sW[0], rU[0], rW[0], xb, r);
+        st_line<T, NP, 1>(sF, xb, r);
         __syncthreads();
-        {
-            T x[NP], gw[NP], gu[NP], f[NP];
-            ld_line<T, NP, 1>(sW[c], xb, x);
-            eo_apply<T, NP>(M.Dg, x, gw);
-            ld_line<T, NP, 1>(sU[c], xb, x);
-            eo_apply<T, NP>(M.Dg, x, gu);
-            eo_apply<T, NP>(M.Dv, gw, f);
+        jac_pass<T, NP, P>(M, sU[c], sW[c], sU[1], sW[1], rU[1], rW[1], yb, r);
+        if (valid) {
 #pragma unroll
-            for (int m = 0; m < NP; ++m) {
-                const int id = xb + m;
-                const T adv = fma(with_ref(rW[0], sW[0][id]), gu[m], with_ref(rU[0], sU[0][id]) * gw[m]);
-                f[m] = (f[m] - adv) + sF[id];
-            }
-            st_line<T, NP, 1>(sF, xb, f);
-        }
-        __syncthreads();
-        {
-            T g[NP], f[NP];
-            ld_line<T, NP, P>(sG1, yb, g);
-            ld_line<T, NP, P>(sF, yb, f);
-            eo_apply_add<T, NP>(M.Dv, g, f);
-            if (valid) {
-                T* o = out + (size_t)c * (NP * NP) + t;
-#pragma unroll
-                for (int m = 0; m < NP; ++m) o[m * NP] = f[m];
-            }
+            for (int m = 0; m < NP; ++m) out[(size_t)c * NP * NP + m * NP] = r[m] + sF[yb + m * P];
         }
         __syncthreads();
     }
 }
 
 template <typename T, int NP>
-__global__ void jact2_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
-    using Tl = Tile<NP>;
-    constexpr int TPE = NP, P = Tl::P, S2 = Tl::S2;
+__global__ void jac2_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int el = threadIdx.x / TPE, t = threadIdx.x % TPE;
-    const int e = blockIdx.x * (blockDim.x / TPE) + el;
-    const bool valid = e < a.nelem;
+    const int el = threadIdx.x / NP, t = threadIdx.x % NP;
+    const int e = blockIdx.x * (blockDim.x / NP) + el;
+    jac2_body<T, NP>(M, a, e, t, el, e < a.nelem, smem_raw);
+}
+
+// Element e (thread t of the element, slot el of the block's shared memory) of a d = 2 J^T apply.
+template <typename T, int NP>
+__device__ __forceinline__ void jact2_body(const OpMats<T, NP>& M, const ElemArgs& a, int e, int t, int el,
+                                        bool valid, unsigned char* smem_raw) {
+    using Tl = Tile<NP>;
+    constexpr int P = Tl::P, S2 = Tl::S2;
     T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)el * tiles_per_elem<2>(OP_JACT) * S2;
     T* sU[2] = {sm, sm + S2};
     T* sZ[2] = {sm + 2 * S2, sm + 3 * S2};
-    T* sG1 = sm + 4 * S2;
-    T* sF = sm + 5 * S2;
+    T* sF = sm + 4 * S2;
     const int ex = e % a.E, ey = e / a.E;
     T rU[2];
 #pragma unroll
@@ -543,88 +408,40 @@ __global__ void jact2_kernel(const __grid_constant__ OpMats<T, NP> M, const Elem
     }
     __syncthreads();
     const int xb = t * P, yb = t;
-    T* out = reinterpret_cast<T*>(a.lvec) + (size_t)e * 2 * (NP * NP);
+    T* out = reinterpret_cast<T*>(a.lvec) + (size_t)e * 2 * (NP * NP) + t;
 #pragma unroll 1
     for (int l = 0; l < 2; ++l) {
-        {   // y: flux q_y, and the y reaction term when l == 1
-            T z[NP], q[NP];
-            ld_line<T, NP, P>(sZ[l], yb, z);
-            eo_apply<T, NP>(M.Vz, z, q);
-#pragma unroll
-            for (int m = 0; m < NP; ++m) q[m] = fma(with_ref(rU[1], sU[1][yb + m * P]), z[m], q[m]);
-            st_line<T, NP, P>(sG1, yb, q);
-            if (l == 1) {
-                T acc[NP], x[NP], g[NP];
-#pragma unroll
-                for (int m = 0; m < NP; ++m) acc[m] = (T)0;
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    ld_line<T, NP, P>(sU[c], yb, x);
-                    eo_apply<T, NP>(M.Dg, x, g);
-#pragma unroll
-                    for (int m = 0; m < NP; ++m) acc[m] = fma(sZ[c][yb + m * P], g[m], acc[m]);
-                }
-#pragma unroll
-                for (int m = 0; m < NP; ++m) acc[m] = -acc[m];
-                st_line<T, NP, P>(sF, yb, acc);
-            }
-        }
+        T r[NP];
+        jact_pass<T, NP, 1, 2>(M, sU, sZ, rU, l, 0, xb, r);
+        st_line<T, NP, 1>(sF, xb, r);
         __syncthreads();
-        {   // x: flux, its divergence, the x reaction term when l == 0
-            T z[NP], q[NP], f[NP];
-            ld_line<T, NP, 1>(sZ[l], xb, z);
-            eo_apply<T, NP>(M.Vz, z, q);
+        jact_pass<T, NP, P, 2>(M, sU, sZ, rU, l, 1, yb, r);
+        if (valid) {
 #pragma unroll
-            for (int m = 0; m < NP; ++m) q[m] = fma(with_ref(rU[0], sU[0][xb + m]), z[m], q[m]);
-            eo_apply<T, NP>(M.Dd, q, f);
-            if (l == 0) {
-                T x[NP], g[NP];
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    ld_line<T, NP, 1>(sU[c], xb, x);
-                    eo_apply<T, NP>(M.Dg, x, g);
-#pragma unroll
-                    for (int m = 0; m < NP; ++m) f[m] = fma(-sZ[c][xb + m], g[m], f[m]);
-                }
-            } else {
-#pragma unroll
-                for (int m = 0; m < NP; ++m) f[m] += sF[xb + m];
-            }
-            st_line<T, NP, 1>(sF, xb, f);
-        }
-        __syncthreads();
-        {
-            T q[NP], f[NP];
-            ld_line<T, NP, P>(sG1, yb, q);
-            ld_line<T, NP, P>(sF, yb, f);
-            eo_apply_add<T, NP>(M.Dd, q, f);
-            if (valid) {
-                T* o = out + (size_t)l * (NP * NP) + t;
-#pragma unroll
-                for (int m = 0; m < NP; ++m) o[m * NP] = f[m];
-            }
+            for (int m = 0; m < NP; ++m) out[(size_t)l * NP * NP + m * NP] = r[m] + sF[yb + m * P];
         }
         __syncthreads();
     }
 }
 
+template <typename T, int NP>
+__global__ void jact2_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int el = threadIdx.x / NP, t = threadIdx.x % NP;
+    const int e = blockIdx.x * (blockDim.x / NP) + el;
+    jact2_body<T, NP>(M, a, e, t, el, e < a.nelem, smem_raw);
+}
+
 // ================================================================== d = 1
 // One thread per element; everything in registers.
 template <typename T, int NP>
-__device__ __forceinline__ T load1(T (&x)[NP], const double* __restrict__ g, int e, const ElemArgs& a,
-                                   bool scale_mult) {
-    const double ref = (RefSub<T>::on && !scale_mult) ? __ldg(g + wrap(e * a.N, a.G)) : 0.0;
+__device__ __forceinline__ T load1(T (&x)[NP], const void* g, int e, const ElemArgs& a, bool scale_mult) {
+    float ref_hi = 0.f, ref_lo = 0.f;
+    if (RefSub<T>::on && !scale_mult) read_pair(a, g, wrap(e * a.N, a.G), ref_hi, ref_lo);
 #pragma unroll
-    for (int i = 0; i < NP; ++i) {
-        const double v = __ldg(g + wrap(e * a.N + i, a.G));
-        if (RefSub<T>::on && !scale_mult) {
-            x[i] = (T)(v - ref);
-        } else {
-            x[i] = (T)v;
-            if (scale_mult && (i == 0 || i == a.N)) x[i] *= (T)0.5;
-        }
-    }
-    return (T)ref;
+    for (int i = 0; i < NP; ++i)
+        x[i] = tile_value<T>(a, g, wrap(e * a.N + i, a.G), scale_mult, (int)(i == 0 || i == a.N), ref_hi, ref_lo);
+    return (T)ref_hi;
 }
 
 template <typename T, int NP>
@@ -635,28 +452,32 @@ __global__ void op1_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemAr
     const T ru = load1<T, NP>(u, a.u, e, a, false);
     if (op == OP_RHS) {
         T g[NP];
-        eo_apply<T, NP>(M.Dg, u, g);
-        eo_apply<T, NP>(M.Dv, g, f);
+        Pre<T, NP> p;
+        pre_add<T, NP>(u, p);
+        eo_apply<false, T, NP>(M.Dg, p, g);
+        eo_apply<true, T, NP>(M.Sv, p, f);
 #pragma unroll
         for (int m = 0; m < NP; ++m) f[m] = fma(-with_ref(ru, u[m]), g[m], f[m]);
     } else if (op == OP_JAC) {
         T w[NP], gu[NP], gw[NP];
         const T rw = load1<T, NP>(w, a.w, e, a, false);
-        eo_apply<T, NP>(M.Dg, u, gu);
-        eo_apply<T, NP>(M.Dg, w, gw);
-        eo_apply<T, NP>(M.Dv, gw, f);
+        Pre<T, NP> p;
+        pre_add<T, NP>(w, p);
+        eo_apply<false, T, NP>(M.Dg, p, gw);
+        eo_apply<true, T, NP>(M.Sv, p, f);
+        eo_apply<false, T, NP>(M.Dg, u, gu);
 #pragma unroll
         for (int m = 0; m < NP; ++m) f[m] -= fma(with_ref(rw, w[m]), gu[m], with_ref(ru, u[m]) * gw[m]);
     } else {
-        T z[NP], q[NP], gu[NP];
+        T z[NP], q[NP], dv[NP], gu[NP];
         load1<T, NP>(z, a.w, e, a, true);
-        eo_apply<T, NP>(M.Vz, z, q);
+        eo_apply<true, T, NP>(M.Svt, z, f);
 #pragma unroll
-        for (int m = 0; m < NP; ++m) q[m] = fma(with_ref(ru, u[m]), z[m], q[m]);
-        eo_apply<T, NP>(M.Dd, q, f);
-        eo_apply<T, NP>(M.Dg, u, gu);
+        for (int m = 0; m < NP; ++m) q[m] = with_ref(ru, u[m]) * z[m];
+        eo_apply<false, T, NP>(M.Dd, q, dv);
+        eo_apply<false, T, NP>(M.Dg, u, gu);
 #pragma unroll
-        for (int m = 0; m < NP; ++m) f[m] = fma(-z[m], gu[m], f[m]);
+        for (int m = 0; m < NP; ++m) f[m] = fma(-z[m], gu[m], f[m] + dv[m]);
     }
     T* o = reinterpret_cast<T*>(a.lvec) + (size_t)e * NP;
 #pragma unroll

@@ -6,27 +6,34 @@
 // pointwise products at the GLL nodes, and a sum over the elements sharing a
 // node (gather-scatter / direct stiffness summation).
 //
-// Reformulation used here (exact up to rounding).  With GLL collocation the element mass B is diagonal and, on a
-// uniform periodic grid, equal in every element that shares a node, so
+// Reformulation used here (exact up to rounding).  With GLL collocation the
+// element mass B is diagonal and, on a uniform periodic grid, equal in every
+// element that shares a node, so
 //   F = M^-1 Q^T r(Qu)   ==   F(node) = (1/k) sum_{e sharing node} r_e / B
 // with k the number of sharing elements (1, 2, 4 or 8).  Dividing the weak
-// residual by B turns D_j^T B D_j into (W^-1 Dhat^T W) Dhat along direction j:
-// every mass factor disappears into 1D matrices.  For the transpose, with
+// residual by B turns the viscous term nu D_j^T B D_j along direction j into
+// the 1D second-derivative matrix Sv = -nu (2/h)^2 W^-1 Dhat^T W Dhat, applied
+// along j: every mass factor folds into 1D matrices.  For the transpose, with
 // zhat = v / k (so B z = zhat for z = M^-1 v):
-//   (L^T z)_l = sum_j Dd_j [ Vz_j zhat_l + U_j zhat_l ] - sum_c zhat_c Dg_l U_c,
-// Vz = nu (2/h) W Dhat W^-1, Dd = -(2/h) Dhat^T, Dg = (2/h) Dhat.
+//   (L^T z)_l = sum_j [ Svt_j zhat_l + Dd_j (U_j zhat_l) ] - sum_c zhat_c Dg_l U_c,
+// Svt = -nu (2/h)^2 Dhat^T W Dhat W^-1, Dd = -(2/h) Dhat^T, Dg = (2/h) Dhat.
 //
-// Every 1D matrix here is centro-antisymmetric (A[n-1-i][n-1-j] = -A[i][j],
-// because the GLL nodes are symmetric), so a contraction of a line of n values
-// costs n^2/2 multiply-adds plus 2n adds (even-odd split) instead of n^2.
+// Dg and Dd are centro-antisymmetric (A[n-1-i][n-1-j] = -A[i][j], because the
+// GLL nodes are symmetric) and Sv, Svt are centro-symmetric (products of two
+// such matrices), so a contraction of a line of n values costs n^2/2
+// multiply-adds plus n adds, with the n pre-adds shared by every matrix
+// applied to the same line (even-odd split).
 //
-// Thread layout: one thread per grid line of an element.  A contraction pass
-// along direction x, y or z lets each thread load its line from a padded
-// shared-memory tile into registers, contract, and store.  d = 3 uses n^2
-// threads per element, d = 2 uses n, d = 1 one thread per element.
+// Thread layout: one thread per grid line of an element.  One pass per
+// direction: each thread loads its line from a padded shared-memory tile,
+// applies every 1D matrix the operator needs along that direction, forms the
+// pointwise terms at the line's nodes and adds its part of the result.  d = 3
+// uses n^2 threads per element, d = 2 uses n, d = 1 one thread per element.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include "df64.cuh"
 
 namespace semk {
 
@@ -34,68 +41,86 @@ namespace semk {
 enum OpKind { OP_RHS = 0, OP_JAC = 1, OP_JACT = 2 };
 
 // ---------------------------------------------------------------- even-odd matrices
-// A centro-antisymmetric n x n matrix A is stored as
-//   e[i][j] = (A[i][j] + A[i][n-1-j]) / 2   (j < H), e[i][H] = A[i][H] (odd n)
+// An n x n matrix A with A[n-1-i][n-1-j] = sigma A[i][j] (sigma = -1: centro-
+// antisymmetric, +1: centro-symmetric) is stored, with H = n/2, as
+//   e[i][j] = (A[i][j] + A[i][n-1-j]) / 2   (j < H),  e[i][H] = A[i][H]  (odd n)
 //   o[i][j] = (A[i][j] - A[i][n-1-j]) / 2   (j < H)
-//   m[j]    =  A[H][j]                      (odd n: middle row, j < H)
-// with H = n/2; then for i < H
-//   y_i = a_i + b_i,  y_{n-1-i} = b_i - a_i,  a = e xe, b = o xo,
-//   xe_j = x_j + x_{n-1-j} (xe_H = x_H), xo_j = x_j - x_{n-1-j},
-// and for odd n y_H = m . xo.
+//   m[j]    =  A[H][j]                      (odd n: middle row, j <= H)
+// Then with the pre-adds xe_j = x_j + x_{n-1-j} (xe_H = x_H), xo_j = x_j - x_{n-1-j}
+// and a = e xe, b = o xo:   y_i = a_i + b_i  and
+//   antisymmetric: y_{n-1-i} = b_i - a_i,  y_H = sum_{j<H} m_j xo_j  (odd n)
+//   symmetric:     y_{n-1-i} = a_i - b_i,  y_H = sum_{j<H} m_j xe_j + m_H x_H.
 template <typename T, int NP>
 struct EOMat {
     static constexpr int H = NP / 2;
     static constexpr int HE = NP / 2 + (NP & 1);
     T e[H][HE];
     T o[H][H];
-    T m[H];
+    T m[H + 1];
 };
 
 template <typename T, int NP>
 struct OpMats {
-    EOMat<T, NP> Dg;  // (2/h) Dhat                       gradient
-    EOMat<T, NP> Dv;  // -nu (2/h) W^-1 Dhat^T W           viscous divergence of a gradient (F, J)
-    EOMat<T, NP> Vz;  // nu (2/h) W Dhat W^-1              viscous flux from zhat (J^T)
-    EOMat<T, NP> Dd;  // -(2/h) Dhat^T                     divergence (J^T)
+    EOMat<T, NP> Dg;   // (2/h) Dhat                                antisymmetric: gradient
+    EOMat<T, NP> Sv;   // -nu (2/h)^2 W^-1 Dhat^T W Dhat             symmetric: viscous term of F and J
+    EOMat<T, NP> Svt;  // -nu (2/h)^2 Dhat^T W Dhat W^-1             symmetric: viscous term of J^T
+    EOMat<T, NP> Dd;   // -(2/h) Dhat^T                              antisymmetric: divergence (J^T)
 };
 
-// y = A x
+// Pre-added halves of one line.
 template <typename T, int NP>
-__device__ __forceinline__ void eo_apply(const EOMat<T, NP>& A, const T (&x)[NP], T (&y)[NP]) {
+struct Pre {
+    T xe[NP / 2 + (NP & 1)];
+    T xo[NP / 2];
+};
+
+template <typename T, int NP>
+__device__ __forceinline__ void pre_add(const T (&x)[NP], Pre<T, NP>& p) {
     constexpr int H = NP / 2;
-    T xe[H + (NP & 1)], xo[H];
 #pragma unroll
     for (int j = 0; j < H; ++j) {
-        xe[j] = x[j] + x[NP - 1 - j];
-        xo[j] = x[j] - x[NP - 1 - j];
+        p.xe[j] = x[j] + x[NP - 1 - j];
+        p.xo[j] = x[j] - x[NP - 1 - j];
     }
-    if constexpr (NP & 1) xe[H] = x[H];
+    if constexpr (NP & 1) p.xe[H] = x[H];
+}
+
+// y = A x for a centro-antisymmetric (SYM = false) or centro-symmetric (SYM = true) A.
+template <bool SYM, typename T, int NP>
+__device__ __forceinline__ void eo_apply(const EOMat<T, NP>& A, const Pre<T, NP>& p, T (&y)[NP]) {
+    constexpr int H = NP / 2;
 #pragma unroll
     for (int i = 0; i < H; ++i) {
-        T a = A.e[i][0] * xe[0];
+        T a = A.e[i][0] * p.xe[0];
 #pragma unroll
-        for (int j = 1; j < H + (NP & 1); ++j) a = fma(A.e[i][j], xe[j], a);
-        T b = A.o[i][0] * xo[0];
+        for (int j = 1; j < H + (NP & 1); ++j) a = fma(A.e[i][j], p.xe[j], a);
+        T b = A.o[i][0] * p.xo[0];
 #pragma unroll
-        for (int j = 1; j < H; ++j) b = fma(A.o[i][j], xo[j], b);
+        for (int j = 1; j < H; ++j) b = fma(A.o[i][j], p.xo[j], b);
         y[i] = a + b;
-        y[NP - 1 - i] = b - a;
+        y[NP - 1 - i] = SYM ? a - b : b - a;
     }
     if constexpr (NP & 1) {
-        T c = A.m[0] * xo[0];
+        if constexpr (SYM) {
+            T c = A.m[H] * p.xe[H];
 #pragma unroll
-        for (int j = 1; j < H; ++j) c = fma(A.m[j], xo[j], c);
-        y[H] = c;
+            for (int j = 0; j < H; ++j) c = fma(A.m[j], p.xe[j], c);
+            y[H] = c;
+        } else {
+            T c = A.m[0] * p.xo[0];
+#pragma unroll
+            for (int j = 1; j < H; ++j) c = fma(A.m[j], p.xo[j], c);
+            y[H] = c;
+        }
     }
 }
 
-// y += A x
-template <typename T, int NP>
-__device__ __forceinline__ void eo_apply_add(const EOMat<T, NP>& A, const T (&x)[NP], T (&y)[NP]) {
-    T t[NP];
-    eo_apply<T, NP>(A, x, t);
-#pragma unroll
-    for (int m = 0; m < NP; ++m) y[m] += t[m];
+// y = A x from the raw line.
+template <bool SYM, typename T, int NP>
+__device__ __forceinline__ void eo_apply(const EOMat<T, NP>& A, const T (&x)[NP], T (&y)[NP]) {
+    Pre<T, NP> p;
+    pre_add<T, NP>(x, p);
+    eo_apply<SYM, T, NP>(A, p, y);
 }
 
 // ---------------------------------------------------------------- tile geometry
@@ -122,11 +147,13 @@ __device__ __forceinline__ void st_line(T* s, int base, const T (&x)[NP]) {
 
 // Launch-time arguments shared by the element kernels.
 struct ElemArgs {
-    const double* u;   // state at which the operator is evaluated (global, SoA)
-    const double* w;   // second input: w for J, v for J^T (unused by F)
+    const void* u;     // state at which the operator is evaluated (global, SoA)
+    const void* w;     // second input: w for J, v for J^T (unused by F)
     void* lvec;        // output: element-local values, [elem][comp][n^d] (unpadded)
     int E, N, G;       // elements per direction, order, unique nodes per direction
     int nelem;         // E^d
+    unsigned plane;    // unknowns per vector: offset of the lo plane of a float-pair input
+    int in_f2;         // FP32 form: inputs are float-pair planes (1) or doubles (0)
 };
 
 // Global index of component c at unique node (gz, gy, gx) of a d-dimensional grid.

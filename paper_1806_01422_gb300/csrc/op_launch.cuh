@@ -9,6 +9,8 @@
 
 namespace semk {
 
+// Even/odd halves of a centro-(anti)symmetric matrix (the storage is the same
+// for both symmetries; the kernels apply the matching reconstruction).
 template <typename T, int NP>
 void split_eo(EOMat<T, NP>& M, const double* A) {
     constexpr int H = NP / 2;
@@ -18,8 +20,8 @@ void split_eo(EOMat<T, NP>& M, const double* A) {
             M.o[i][j] = (T)(0.5 * (A[i * NP + j] - A[i * NP + (NP - 1 - j)]));
         }
         if (NP & 1) M.e[i][H] = (T)A[i * NP + H];
-        M.m[i] = (NP & 1) ? (T)A[H * NP + i] : (T)0;
     }
+    for (int j = 0; j <= H; ++j) M.m[j] = (NP & 1) ? (T)A[H * NP + j] : (T)0;
 }
 
 constexpr int SMEM_TARGET = 100 * 1024;   // two blocks per SM fit in 227 KB
@@ -36,8 +38,8 @@ template <typename T, int D, int NP>
 cudaError_t launch_elem_np(int op, const double* mats, const ElemArgs& a, cudaStream_t s) {
     OpMats<T, NP> M;
     split_eo<T, NP>(M.Dg, mats + 0 * NP * NP);
-    split_eo<T, NP>(M.Dv, mats + 1 * NP * NP);
-    split_eo<T, NP>(M.Vz, mats + 2 * NP * NP);
+    split_eo<T, NP>(M.Sv, mats + 1 * NP * NP);
+    split_eo<T, NP>(M.Svt, mats + 2 * NP * NP);
     split_eo<T, NP>(M.Dd, mats + 3 * NP * NP);
     if (a.nelem <= 0) return cudaSuccess;
     if constexpr (D == 1) {
@@ -64,8 +66,19 @@ cudaError_t launch_elem_np(int op, const double* mats, const ElemArgs& a, cudaSt
         else
             k = op == OP_RHS ? rhs2_kernel<T, NP> : (op == OP_JAC ? jac2_kernel<T, NP> : jact2_kernel<T, NP>);
         if (smem > 48 * 1024) {
-            cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (err != cudaSuccess) return err;
+            // once per kernel, size and device (no API call in the launch path afterwards,
+            // so launches can be recorded into a CUDA graph)
+            static thread_local unsigned long long done[3][3] = {};
+            static thread_local size_t done_smem[3][3] = {};
+            int dev = 0;
+            cudaGetDevice(&dev);
+            const unsigned long long bit = 1ull << (dev & 63);
+            if (!(done[op][0] & bit) || done_smem[op][0] < smem) {
+                cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (err != cudaSuccess) return err;
+                done[op][0] |= bit;
+                done_smem[op][0] = smem;
+            }
         }
         k<<<blocks, threads, smem, s>>>(M, a);
         return cudaGetLastError();

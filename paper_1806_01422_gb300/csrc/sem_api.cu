@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <algorithm>
+
 #include "host_tables.h"
 #include "sem.h"
 #include "sem_internal.h"
@@ -80,7 +82,30 @@ bool tableau_of(int scheme, Tableau& t) {
 
 }  // namespace
 
+// Host state of a batch of independent 2D instances (sem_batch_create).
+struct BatchHost {
+    int count = 0;
+    std::vector<BatchInst> inst;
+    std::vector<unsigned char> mats;   // packed OpMats<double, NP> per instance
+    std::vector<RowInfo> rows;
+    std::vector<int> row_start;        // count + 1
+    std::vector<double> J;             // per-instance misfit of the last evaluation
+    // device copies (allocated on first use)
+    BatchInst* d_inst = nullptr;
+    unsigned char* d_mats = nullptr;
+    RowInfo* d_rows = nullptr;
+    int* d_row_start = nullptr;
+    WorkItem* d_items = nullptr;
+    int nitems = 0;
+    double* d_J = nullptr;
+    double* d_rowpart = nullptr;
+    int threads = 0;                   // block size of the element kernel (autotuned)
+    int blocks = 0;
+    double tune_ms[8] = {0};
+};
+
 struct sem_ctx {
+    BatchHost* batch = nullptr;
     int dim = 0, E = 0, N = 0, np = 0, G = 0;
     int precision = SEM_PREC_FP64, ckpt_mode = SEM_CKPT_AUTO, ckpt_slots = 0;
     size_t ckpt_budget = 0;
@@ -102,6 +127,20 @@ struct sem_ctx {
     double f_dt = 0;
     std::vector<int> f_ckpt;
     long long st[3] = {0, 0, 0};  // forward F applies, adjoint F applies, adjoint J^T applies
+    // CUDA graph of one gradient evaluation (sem_set_graph), keyed on its arguments
+    bool graph_on = false;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    struct GraphKey {
+        int scheme, nsteps;
+        double dt;
+        const void *u0, *uo, *grad;
+        bool operator==(const GraphKey& o) const {
+            return scheme == o.scheme && nsteps == o.nsteps && dt == o.dt && u0 == o.u0 && uo == o.uo && grad == o.grad;
+        }
+    } graph_key{-1, 0, 0.0, nullptr, nullptr, nullptr};
+    long long graph_replays = 0;
+    int fixed_mode = -1, fixed_slots = 0;   // storage mode fixed before a graph recording
     // opt-in kernel timing: event pairs per launch, drained when the pool fills
     int prof = 0;                 // 0: off; n: time one apply in n per kind
     long long prof_tick[4] = {0, 0, 0, 0};
@@ -115,7 +154,13 @@ struct sem_ctx {
 namespace {
 
 // work vector roles inside sem_ctx::vecs
-enum { V_K0 = 0, V_STAGE0 = 4, V_CUR0 = 7, V_CUR1 = 8, V_NU = 9, V_UN = 10, NVEC = 11 };
+enum { V_K0 = 0, V_STAGE0 = 4, V_CUR0 = 7, V_CUR1 = 8, V_NU = 9, V_UN = 10, V_LAM = 11, NVEC = 12 };
+
+// FP32 form: every sweep-internal state is a pair of FP32 planes (hi at [0, ndof),
+// lo at [ndof, 2 ndof) floats), the same bytes as one double state.
+bool f32(sem_t h) { return h->precision == SEM_PREC_FP32_BULK; }
+float* fl(double* p) { return reinterpret_cast<float*>(p); }
+const float* fl(const double* p) { return reinterpret_cast<const float*>(p); }
 
 double* vec(sem_t h, int i) { return h->vecs + (size_t)i * h->ndof; }
 
@@ -219,11 +264,17 @@ int prof_end(sem_t h, long long slot, cudaStream_t s) {
 }
 
 // One operator apply: element kernel into the element-local buffer, then the
-// gather-scatter sum with the given epilogue.
-int apply(sem_t h, int op, const double* u, const double* w, const Epi& ep, cudaStream_t s) {
+// gather-scatter sum with the given epilogue.  f2_in: the inputs are
+// sweep-internal float-pair states (FP32 form), not caller doubles.
+int batch_apply(sem_t h, int op, const double* u, const double* w, const Epi& ep, cudaStream_t s);
+
+int apply(sem_t h, int op, const double* u, const double* w, const Epi& ep, cudaStream_t s, bool f2_in = false) {
+    if (h->batch) return batch_apply(h, op, u, w, ep, s);
     ElemArgs a;
     a.u = u;
     a.w = w;
+    a.plane = (unsigned)h->ndof;
+    a.in_f2 = f2_in ? 1 : 0;
     a.lvec = h->lvec;
     a.E = h->E;
     a.N = h->N;
@@ -284,6 +335,7 @@ int rk_stages(sem_t h, const Tableau& T, double dt, const double* un, double* co
         Epi ep;
         std::memset(&ep, 0, sizeof(ep));
         ep.nonfinite = h->flag;
+        ep.f2 = f32(h);
         const int su = add_src(ep, un);
         if (i < T.s - 1) {
             ep.out[0] = Y[i + 1];
@@ -302,7 +354,7 @@ int rk_stages(sem_t h, const Tableau& T, double dt, const double* un, double* co
                 if (T.b[j] != 0.0) ep.beta[0][add_src(ep, vec(h, V_K0 + j))] = dt * T.b[j];
             ep.nout = 1;
         }
-        SEM_TRY(apply(h, OP_RHS, Yi, nullptr, ep, s));
+        SEM_TRY(apply(h, OP_RHS, Yi, nullptr, ep, s, f32(h)));
         ++count;
     }
     return SEM_OK;
@@ -321,6 +373,7 @@ int rk_adjoint_step(sem_t h, const Tableau& T, double dt, const double* const* Y
         Epi ep;
         std::memset(&ep, 0, sizeof(ep));
         ep.nonfinite = h->flag;
+        ep.f2 = f32(h);
         const int sl = add_src(ep, lam);
         if (i > 0) {
             ep.out[0] = nu;
@@ -342,7 +395,7 @@ int rk_adjoint_step(sem_t h, const Tableau& T, double dt, const double* const* Y
             for (int m = 0; m < ep.nsrc; ++m) ep.beta[1][m] = c * ep.beta[0][m];
             ep.nout = 2;
         }
-        SEM_TRY(apply(h, OP_JACT, Y[i], nu, ep, s));
+        SEM_TRY(apply(h, OP_JACT, Y[i], nu, ep, s, f32(h)));
         ++count;
     }
     return SEM_OK;
@@ -372,6 +425,11 @@ int alloc_traj(sem_t h, size_t nvec) {
 
 // Storage mode for a sweep of nsteps steps of an s-stage scheme.
 int choose_mode(sem_t h, int s, int nsteps, int& mode, int& slots) {
+    if (h->fixed_mode >= 0) {
+        mode = h->fixed_mode;
+        slots = h->fixed_slots;
+        return SEM_OK;
+    }
     mode = h->ckpt_mode;
     slots = h->ckpt_slots;
     if (mode != SEM_CKPT_AUTO) return SEM_OK;
@@ -407,7 +465,10 @@ int check_flag(sem_t h, cudaStream_t s, const char* what) {
     return SEM_OK;
 }
 
-int forward_impl(sem_t h, int scheme, double dt, int nsteps, const double* u0, double* uT, cudaStream_t s) {
+// uT_internal: uT is a handle work state (float pairs in the FP32 form) rather
+// than the caller's double output.
+int forward_impl(sem_t h, int scheme, double dt, int nsteps, const double* u0, double* uT, cudaStream_t s,
+                 bool uT_internal = false) {
     Tableau T;
     if (!tableau_of(scheme, T)) return fail(SEM_ERR_ARG, "unknown RK scheme %d", scheme);
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(SEM_ERR_ARG, "dt must be finite and > 0");
@@ -426,8 +487,21 @@ int forward_impl(sem_t h, int scheme, double dt, int nsteps, const double* u0, d
     double* Yw[4] = {nullptr, vec(h, V_STAGE0), vec(h, V_STAGE0 + 1), vec(h, V_STAGE0 + 2)};
     long long count = 0;
     std::vector<int> ckpt;
+    // the final state: in the FP32 form it is produced as float pairs and widened at the end
+    double* const uT_caller = uT;
+    const bool widen_out = f32(h) && !uT_internal;
+    if (widen_out) uT = vec(h, V_UN);
+    auto put_u0 = [&](double* dst) -> int {
+        if (f32(h)) {
+            cudaError_t e = launch_f64_to_f2(u0, fl(dst), h->ndof, s);
+            if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "conversion launch: %s", cudaGetErrorString(e));
+        } else {
+            SEM_CK(cudaMemcpyAsync(dst, u0, vb, cudaMemcpyDeviceToDevice, s));
+        }
+        return SEM_OK;
+    };
     if (mode == SEM_CKPT_STAGES) {
-        SEM_CK(cudaMemcpyAsync(h->traj, u0, vb, cudaMemcpyDeviceToDevice, s));
+        SEM_TRY(put_u0(h->traj));
         for (int n = 0; n < nsteps; ++n) {
             double* base = h->traj + (size_t)n * T.s * h->ndof;
             double* Y[4] = {base, base + h->ndof, base + 2 * h->ndof, base + 3 * h->ndof};
@@ -435,7 +509,7 @@ int forward_impl(sem_t h, int scheme, double dt, int nsteps, const double* u0, d
             SEM_TRY(rk_stages(h, T, dt, base, Y, next, s, count));
         }
     } else if (mode == SEM_CKPT_STATES) {
-        SEM_CK(cudaMemcpyAsync(h->traj, u0, vb, cudaMemcpyDeviceToDevice, s));
+        SEM_TRY(put_u0(h->traj));
         for (int n = 0; n < nsteps; ++n) {
             const double* un = h->traj + (size_t)n * h->ndof;
             double* next = n + 1 < nsteps ? h->traj + (size_t)(n + 1) * h->ndof : uT;
@@ -444,7 +518,7 @@ int forward_impl(sem_t h, int scheme, double dt, int nsteps, const double* u0, d
     } else {
         semh::CkptPlanner P(nsteps, slots);
         ckpt = P.forward_checkpoints(nsteps, slots);
-        SEM_CK(cudaMemcpyAsync(h->traj, u0, vb, cudaMemcpyDeviceToDevice, s));
+        SEM_TRY(put_u0(h->traj));
         const double* cur = h->traj;
         size_t k = 1;
         for (int n = 0; n < nsteps; ++n) {
@@ -455,6 +529,10 @@ int forward_impl(sem_t h, int scheme, double dt, int nsteps, const double* u0, d
             SEM_TRY(rk_stages(h, T, dt, cur, Yw, next, s, count));
             cur = next;
         }
+    }
+    if (widen_out) {
+        cudaError_t e = launch_f2_to_f64(fl(uT), uT_caller, h->ndof, s);
+        if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "conversion launch: %s", cudaGetErrorString(e));
     }
     h->have_fwd = true;
     h->f_scheme = scheme;
@@ -467,9 +545,10 @@ int forward_impl(sem_t h, int scheme, double dt, int nsteps, const double* u0, d
     return SEM_OK;
 }
 
-int adjoint_impl(sem_t h, const double* lamT, double* lam0, cudaStream_t s) {
+// lam_internal (FP32 form only): the terminal adjoint is already in vec(V_LAM).
+int adjoint_impl(sem_t h, const double* lamT, double* lam0, cudaStream_t s, bool lam_internal = false) {
     if (!h->have_fwd) return fail(SEM_ERR_STATE, "sem_rk_adjoint needs a completed sem_rk_forward");
-    SEM_TRY(check_state_ptr(lamT, "lamT"));
+    if (!lam_internal) SEM_TRY(check_state_ptr(lamT, "lamT"));
     SEM_TRY(check_state_ptr(lam0, "lam0"));
     if (lamT != lam0 && overlap(lamT, lam0, vec_bytes(h))) return fail(SEM_ERR_ALIAS, "lam0 partially overlaps lamT");
     Tableau T;
@@ -477,8 +556,18 @@ int adjoint_impl(sem_t h, const double* lamT, double* lam0, cudaStream_t s) {
     const double dt = h->f_dt;
     const int nsteps = h->f_nsteps;
     const size_t vb = vec_bytes(h);
-    if (lam0 != lamT) SEM_CK(cudaMemcpyAsync(lam0, lamT, vb, cudaMemcpyDeviceToDevice, s));
-    {
+    double* const lam_out = lam0;
+    if (f32(h)) {
+        // the adjoint runs on float pairs in vec(V_LAM); lam0 is written at the end
+        lam0 = vec(h, V_LAM);
+        if (!lam_internal) {
+            cudaError_t e = launch_f64_to_f2(lamT, fl(lam0), h->ndof, s);
+            if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "conversion launch: %s", cudaGetErrorString(e));
+        }
+        cudaError_t e = launch_scale_f2(fl(vec(h, V_NU)), fl(lam0), dt * T.b[T.s - 1], h->ndof, s);
+        if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "scale launch: %s", cudaGetErrorString(e));
+    } else {
+        if (lam0 != lamT) SEM_CK(cudaMemcpyAsync(lam0, lamT, vb, cudaMemcpyDeviceToDevice, s));
         cudaError_t e = launch_scale(vec(h, V_NU), lam0, dt * T.b[T.s - 1], h->ndof, s);
         if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "scale launch: %s", cudaGetErrorString(e));
     }
@@ -521,12 +610,20 @@ int adjoint_impl(sem_t h, const double* lamT, double* lam0, cudaStream_t s) {
             }
         }
     }
+    if (f32(h)) {
+        cudaError_t e = launch_f2_to_f64(fl(lam0), lam_out, h->ndof, s);
+        if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "conversion launch: %s", cudaGetErrorString(e));
+    }
     h->st[1] = nrhs;
     h->st[2] = njt;
     return SEM_OK;
 }
 
-int objective_impl(sem_t h, const double* u, const double* uo, double* lam, cudaStream_t s) {
+// f2_state (FP32 form): u and lam are float-pair work states.
+int batch_objective(sem_t h, const double* u, const double* uo, double* lam, cudaStream_t s);
+
+int objective_impl(sem_t h, const double* u, const double* uo, double* lam, cudaStream_t s, bool f2_state = false) {
+    if (h->batch) return batch_objective(h, u, uo, lam, s);
     ObjArgs a;
     std::memset(&a, 0, sizeof(a));
     a.D = h->dim;
@@ -537,9 +634,136 @@ int objective_impl(sem_t h, const double* u, const double* uo, double* lam, cuda
     for (int i = 0; i < h->N; ++i) a.mw[i] = h->mw[i];
     a.scale = std::pow(h->h / 2.0, h->dim);
     const int nb = objective_blocks(a.ndof);
-    cudaError_t e = launch_objective(u, uo, lam, h->partials, nb, a, s);
+    cudaError_t e = f2_state ? launch_objective_f2(fl(u), uo, fl(lam), h->partials, nb, a, s)
+                             : launch_objective(u, uo, lam, h->partials, nb, a, s);
     if (e == cudaSuccess) e = launch_sum_partials(h->partials, nb, h->scal, 0.5, s);
     if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "objective launch: %s", cudaGetErrorString(e));
+    return SEM_OK;
+}
+
+// ------------------------------------------------------------------ batches
+template <typename T>
+int upload(T** dst, const std::vector<T>& src) {
+    cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * std::max<size_t>(src.size(), 1));
+    if (e == cudaSuccess && !src.empty())
+        e = cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? SEM_ERR_OOM : SEM_ERR_CUDA, "batch tables: %s",
+                    cudaGetErrorString(e));
+    }
+    return SEM_OK;
+}
+
+// Work items for a block size: each instance's elements in chunks of threads / NP.
+int batch_items(sem_t h, int threads) {
+    BatchHost* b = h->batch;
+    std::vector<WorkItem> items;
+    for (int k = 0; k < b->count; ++k) {
+        const BatchInst& in = b->inst[k];
+        const int epb = threads / in.NP;
+        for (int e0 = 0; e0 < in.nelem; e0 += epb) items.push_back({k, e0, std::min(epb, in.nelem - e0), in.NP});
+    }
+    cudaFree(b->d_items);
+    b->d_items = nullptr;
+    SEM_TRY(upload(&b->d_items, items));
+    b->nitems = (int)items.size();
+    b->threads = threads;
+    const size_t smem = batch_elem_smem(threads, OP_JAC);
+    int per_sm = std::min<int>(2048 / threads, (int)((227u * 1024u) / std::max<size_t>(smem, 1)));
+    per_sm = std::max(1, per_sm);
+    b->blocks = std::max(1, std::min(b->nitems, 152 * per_sm));
+    return SEM_OK;
+}
+
+BatchDev batch_dev(sem_t h) {
+    BatchHost* b = h->batch;
+    BatchDev d;
+    d.inst = b->d_inst;
+    d.items = b->d_items;
+    d.nitems = b->nitems;
+    d.rows = b->d_rows;
+    d.nrows = (int)b->rows.size();
+    d.mats = b->d_mats;
+    return d;
+}
+
+int batch_tables(sem_t h) {
+    BatchHost* b = h->batch;
+    if (b->d_inst) return SEM_OK;
+    SEM_TRY(upload(&b->d_inst, b->inst));
+    SEM_TRY(upload(&b->d_mats, b->mats));
+    SEM_TRY(upload(&b->d_rows, b->rows));
+    SEM_TRY(upload(&b->d_row_start, b->row_start));
+    std::vector<double> zeros(b->count + 1, 0.0), rz(b->rows.size(), 0.0);
+    SEM_TRY(upload(&b->d_J, zeros));
+    SEM_TRY(upload(&b->d_rowpart, rz));
+    return SEM_OK;
+}
+
+// Autotuner: time the batched J^T element pass (the most expensive) for each
+// candidate block size and keep the fastest.  Synchronises `s`.
+int batch_tune(sem_t h, cudaStream_t s) {
+    BatchHost* b = h->batch;
+    SEM_TRY(batch_tables(h));
+    const int cand[4] = {64, 128, 192, 256};
+    cudaEvent_t e0, e1;
+    SEM_CK(cudaEventCreate(&e0));
+    SEM_CK(cudaEventCreate(&e1));
+    SEM_CK(cudaMemsetAsync(vec(h, V_CUR0), 0, 2 * vec_bytes(h), s));
+    int best = 128;
+    float best_ms = 1e30f;
+    for (int ci = 0; ci < 4; ++ci) {
+        SEM_TRY(batch_items(h, cand[ci]));
+        const BatchDev d = batch_dev(h);
+        const size_t smem = batch_elem_smem(cand[ci], OP_JACT);
+        float tot = 0.f;
+        for (int rep = 0; rep < 4; ++rep) {
+            SEM_CK(cudaEventRecord(e0, s));
+            cudaError_t e = launch_batch_elem(d, OP_JACT, vec(h, V_CUR0), vec(h, V_CUR1), (double*)h->lvec,
+                                              cand[ci], b->blocks, smem, s);
+            if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "batched element kernel: %s", cudaGetErrorString(e));
+            SEM_CK(cudaEventRecord(e1, s));
+            SEM_CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            SEM_CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) tot += ms;
+        }
+        b->tune_ms[ci] = tot / 3;
+        if (tot < best_ms) {
+            best_ms = tot;
+            best = cand[ci];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return batch_items(h, best);
+}
+
+int batch_apply(sem_t h, int op, const double* u, const double* w, const Epi& ep, cudaStream_t s) {
+    BatchHost* b = h->batch;
+    SEM_TRY(batch_tables(h));
+    if (!b->threads) SEM_TRY(batch_tune(h, s));
+    const BatchDev d = batch_dev(h);
+    long long slot;
+    SEM_TRY(prof_begin(h, op, s, slot));
+    cudaError_t e = launch_batch_elem(d, op, u, w, (double*)h->lvec, b->threads, b->blocks,
+                                      batch_elem_smem(b->threads, op), s);
+    if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "batched element kernel: %s", cudaGetErrorString(e));
+    SEM_TRY(prof_end(h, slot, s));
+    SEM_TRY(prof_begin(h, 3, s, slot));
+    e = launch_batch_assemble(d, (const double*)h->lvec, op != OP_JACT, ep, s);
+    if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "batched assembly: %s", cudaGetErrorString(e));
+    SEM_TRY(prof_end(h, slot, s));
+    return SEM_OK;
+}
+
+int batch_objective(sem_t h, const double* u, const double* uo, double* lam, cudaStream_t s) {
+    BatchHost* b = h->batch;
+    SEM_TRY(batch_tables(h));
+    cudaError_t e = launch_batch_objective(batch_dev(h), u, uo, lam, b->d_rowpart, b->d_row_start, b->count,
+                                           b->d_J, h->scal, s);
+    if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "batched misfit: %s", cudaGetErrorString(e));
     return SEM_OK;
 }
 
@@ -601,12 +825,25 @@ void sem_destroy(sem_t h) {
         cudaEventDestroy(h->ev_start[i]);
         cudaEventDestroy(h->ev_stop[i]);
     }
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph_stream) cudaStreamDestroy(h->graph_stream);
     cudaFree(h->lvec);
     cudaFree(h->partials);
     cudaFree(h->scal);
     cudaFree(h->flag);
     cudaFree(h->vecs);
     cudaFree(h->traj);
+    if (h->batch) {
+        BatchHost* b = h->batch;
+        cudaFree(b->d_inst);
+        cudaFree(b->d_mats);
+        cudaFree(b->d_rows);
+        cudaFree(b->d_row_start);
+        cudaFree(b->d_items);
+        cudaFree(b->d_J);
+        cudaFree(b->d_rowpart);
+        delete b;
+    }
     delete h;
 }
 
@@ -614,11 +851,23 @@ size_t sem_ndof(sem_t h) { return h ? h->ndof : 0; }
 
 int sem_coords(sem_t h, double* x) {
     if (!h || !x) return fail(SEM_ERR_ARG, "null handle or output");
+    if (h->batch) return fail(SEM_ERR_ARG, "sem_coords: use sem_batch_coords for a batch handle");
     for (int g = 0; g < h->G; ++g) {
         const int e = g / h->N, i = g % h->N;
         x[g] = e * h->h + (h->xi[i] + 1.0) * h->h / 2.0;
     }
     return SEM_OK;
+}
+
+// FP32 form, standalone apply: the caller's doubles become float pairs once
+// (integer split, one pass over the unknowns) so that the element kernel reads
+// pair planes; the result is widened back to doubles by the assembly.
+static int standalone(sem_t h, int op, const double* u, const double* w, double* out, cudaStream_t s) {
+    if (!f32(h)) return apply(h, op, u, w, epi_plain(out, nullptr), s);
+    cudaError_t e = launch_f64_to_f2(u, fl(vec(h, V_CUR0)), h->ndof, s);
+    if (e == cudaSuccess && w) e = launch_f64_to_f2(w, fl(vec(h, V_CUR1)), h->ndof, s);
+    if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "conversion launch: %s", cudaGetErrorString(e));
+    return apply(h, op, vec(h, V_CUR0), w ? vec(h, V_CUR1) : nullptr, epi_plain(out, nullptr), s, true);
 }
 
 int sem_rhs(sem_t h, const double* u, double* f, void* stream) {
@@ -627,7 +876,7 @@ int sem_rhs(sem_t h, const double* u, double* f, void* stream) {
     SEM_TRY(check_state_ptr(f, "f"));
     if (overlap(u, f, vec_bytes(h))) return fail(SEM_ERR_ALIAS, "f overlaps u");
     SEM_TRY(ensure_workspace(h));
-    return apply(h, OP_RHS, u, nullptr, epi_plain(f, nullptr), (cudaStream_t)stream);
+    return standalone(h, OP_RHS, u, nullptr, f, (cudaStream_t)stream);
 }
 
 int sem_jac_apply(sem_t h, const double* u, const double* w, double* jw, void* stream) {
@@ -637,7 +886,7 @@ int sem_jac_apply(sem_t h, const double* u, const double* w, double* jw, void* s
     SEM_TRY(check_state_ptr(jw, "jw"));
     if (overlap(u, jw, vec_bytes(h)) || overlap(w, jw, vec_bytes(h))) return fail(SEM_ERR_ALIAS, "jw overlaps an input");
     SEM_TRY(ensure_workspace(h));
-    return apply(h, OP_JAC, u, w, epi_plain(jw, nullptr), (cudaStream_t)stream);
+    return standalone(h, OP_JAC, u, w, jw, (cudaStream_t)stream);
 }
 
 int sem_jacT_apply(sem_t h, const double* u, const double* v, double* jtv, void* stream) {
@@ -647,7 +896,7 @@ int sem_jacT_apply(sem_t h, const double* u, const double* v, double* jtv, void*
     SEM_TRY(check_state_ptr(jtv, "jtv"));
     if (overlap(u, jtv, vec_bytes(h)) || overlap(v, jtv, vec_bytes(h))) return fail(SEM_ERR_ALIAS, "jtv overlaps an input");
     SEM_TRY(ensure_workspace(h));
-    return apply(h, OP_JACT, u, v, epi_plain(jtv, nullptr), (cudaStream_t)stream);
+    return standalone(h, OP_JACT, u, v, jtv, (cudaStream_t)stream);
 }
 
 int sem_rk_forward(sem_t h, int scheme, double dt, int nsteps, const double* u0, double* uT, void* stream) {
@@ -683,20 +932,78 @@ int sem_objective(sem_t h, const double* u, const double* uo, double* J_host, do
     return SEM_OK;
 }
 
+// The launch sequence of one gradient evaluation (no host synchronisation inside).
+static int objective_grad_launches(sem_t h, int scheme, double dt, int nsteps, const double* u0, const double* uo,
+                                   double* grad, cudaStream_t s) {
+    double* uN = vec(h, V_UN);
+    SEM_CK(cudaMemsetAsync(h->flag, 0, sizeof(unsigned), s));
+    SEM_TRY(forward_impl(h, scheme, dt, nsteps, u0, uN, s, true));
+    if (f32(h)) {
+        SEM_TRY(objective_impl(h, uN, uo, vec(h, V_LAM), s, true));
+        SEM_TRY(adjoint_impl(h, nullptr, grad, s, true));
+    } else {
+        SEM_TRY(objective_impl(h, uN, uo, grad, s));
+        SEM_TRY(adjoint_impl(h, grad, grad, s));
+    }
+    return SEM_OK;
+}
+
+// Record the gradient evaluation into a CUDA graph on a private stream (after
+// every allocation it needs), then replay it on `s` while the arguments match.
+static int objective_grad_graph(sem_t h, int scheme, double dt, int nsteps, const double* u0, const double* uo,
+                                double* grad, cudaStream_t s) {
+    sem_ctx::GraphKey key{scheme, nsteps, dt, u0, uo, grad};
+    if (!h->graph_exec || !(h->graph_key == key)) {
+        Tableau T;
+        if (!tableau_of(scheme, T)) return fail(SEM_ERR_ARG, "unknown RK scheme %d", scheme);
+        int mode, slots;
+        SEM_TRY(choose_mode(h, T.s, nsteps, mode, slots));
+        if (mode == SEM_CKPT_BINOMIAL && slots > nsteps) slots = nsteps;
+        SEM_TRY(alloc_traj(h, mode == SEM_CKPT_STAGES ? (size_t)nsteps * T.s
+                                 : (mode == SEM_CKPT_STATES ? (size_t)nsteps : (size_t)slots)));
+        if (h->batch && !h->batch->threads) SEM_TRY(batch_tune(h, s));
+        if (!h->graph_stream) SEM_CK(cudaStreamCreateWithFlags(&h->graph_stream, cudaStreamNonBlocking));
+        SEM_CK(cudaStreamSynchronize(s));
+        const int prof = h->prof;
+        h->prof = 0;
+        h->fixed_mode = mode;
+        h->fixed_slots = slots;
+        cudaGraph_t g = nullptr;
+        SEM_CK(cudaStreamBeginCapture(h->graph_stream, cudaStreamCaptureModeThreadLocal));
+        const int rc = objective_grad_launches(h, scheme, dt, nsteps, u0, uo, grad, h->graph_stream);
+        cudaError_t ec = cudaStreamEndCapture(h->graph_stream, &g);
+        h->prof = prof;
+        h->fixed_mode = -1;
+        if (rc != SEM_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (ec != cudaSuccess) return fail(SEM_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ec));
+        if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+        ec = cudaGraphInstantiate(&h->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ec != cudaSuccess) return fail(SEM_ERR_CUDA, "graph instantiation: %s", cudaGetErrorString(ec));
+        h->graph_key = key;
+    }
+    SEM_CK(cudaGraphLaunch(h->graph_exec, s));
+    ++h->graph_replays;
+    return SEM_OK;
+}
+
 int sem_objective_grad(sem_t h, int scheme, double dt, int nsteps, const double* u0, const double* uo,
                        double* J_host, double* grad, void* stream) {
     if (!h || !J_host) return fail(SEM_ERR_ARG, "null handle or J_host");
+    SEM_TRY(check_state_ptr(u0, "u0"));
     SEM_TRY(check_state_ptr(uo, "u_obs"));
     SEM_TRY(check_state_ptr(grad, "grad"));
     if (overlap(grad, u0, vec_bytes(h)) || overlap(grad, uo, vec_bytes(h)))
         return fail(SEM_ERR_ALIAS, "grad overlaps an input");
+    if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 1) return fail(SEM_ERR_ARG, "dt > 0 and nsteps >= 1");
     SEM_TRY(ensure_workspace(h));
     cudaStream_t s = (cudaStream_t)stream;
-    double* uN = vec(h, V_UN);
-    SEM_CK(cudaMemsetAsync(h->flag, 0, sizeof(unsigned), s));
-    SEM_TRY(forward_impl(h, scheme, dt, nsteps, u0, uN, s));
-    SEM_TRY(objective_impl(h, uN, uo, grad, s));
-    SEM_TRY(adjoint_impl(h, grad, grad, s));
+    if (h->graph_on) SEM_TRY(objective_grad_graph(h, scheme, dt, nsteps, u0, uo, grad, s));
+    else SEM_TRY(objective_grad_launches(h, scheme, dt, nsteps, u0, uo, grad, s));
     unsigned f = 0;
     SEM_CK(cudaMemcpyAsync(J_host, h->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
     SEM_CK(cudaMemcpyAsync(&f, h->flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
@@ -704,6 +1011,19 @@ int sem_objective_grad(sem_t h, int scheme, double dt, int nsteps, const double*
     if (f || !std::isfinite(*J_host)) return fail(SEM_ERR_NONFINITE, "non-finite values in the gradient evaluation");
     return SEM_OK;
 }
+
+int sem_set_graph(sem_t h, int enable) {
+    if (!h) return fail(SEM_ERR_ARG, "null handle");
+    h->graph_on = enable != 0;
+    if (!h->graph_on && h->graph_exec) {
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+        h->graph_key = sem_ctx::GraphKey{-1, 0, 0.0, nullptr, nullptr, nullptr};
+    }
+    return SEM_OK;
+}
+
+long long sem_graph_replays(sem_t h) { return h ? h->graph_replays : -1; }
 
 int sem_ckpt_plan(int nsteps, int slots, long long* advances) {
     if (nsteps < 1 || slots < 0 || !advances) return fail(SEM_ERR_ARG, "nsteps >= 1, slots >= 0, advances != null");
@@ -737,6 +1057,135 @@ int sem_profile_read(sem_t h, double* ms4, long long* count4, int reset) {
             h->prof_n[i] = 0;
         }
     }
+    return SEM_OK;
+}
+
+int sem_batch_create(int count, const int* E, const int* N, const double* nu, const sem_opts* common,
+                     sem_t* out) {
+    if (!out) return fail(SEM_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (count < 1 || !E || !N || !nu) return fail(SEM_ERR_ARG, "count >= 1 and non-null E, N, nu");
+    const int precision = common ? common->precision : SEM_PREC_FP64;
+    if (precision != SEM_PREC_FP64) return fail(SEM_ERR_ARG, "batches support the FP64 form");
+    const double Lbox = (common && common->L > 0) ? common->L : 1.0;
+    BatchHost* b = new BatchHost();
+    b->count = count;
+    size_t off = 0, loff = 0, nel = 0;
+    for (int k = 0; k < count; ++k) {
+        const int np = N[k] + 1;
+        if (E[k] < 1 || !batch_np_supported(np) || !(nu[k] >= 0.0) || !std::isfinite(nu[k]) ||
+            (long long)E[k] * N[k] > 65535) {
+            delete b;
+            return fail(SEM_ERR_ARG, "instance %d: need E >= 1, N in {3, 5, 7, 9}, finite nu >= 0 (got E=%d N=%d)", k,
+                        E[k], N[k]);
+        }
+        BatchInst in;
+        std::memset(&in, 0, sizeof(in));
+        in.E = E[k];
+        in.N = N[k];
+        in.NP = np;
+        in.G = E[k] * N[k];
+        in.nelem = E[k] * E[k];
+        in.GD = (unsigned)in.G * in.G;
+        in.off = (unsigned)off;
+        in.loff = loff;
+        const double hk = Lbox / E[k];
+        std::vector<double> xi, w, Dh, mats;
+        semh::gll(N[k], xi, w);
+        semh::derivative(xi, Dh);
+        semh::kernel_matrices(w, Dh, hk, nu[k], mats);
+        for (int i = 0; i < N[k]; ++i) in.mw[i] = w[i];
+        in.mw[0] = w[0] + w[N[k]];
+        in.scale = (hk / 2.0) * (hk / 2.0);
+        for (in.divN_shift = 16; in.divN_shift <= 31; ++in.divN_shift) {
+            in.divN_mul = (unsigned)(((1ull << in.divN_shift) + N[k] - 1) / N[k]);
+            bool ok = true;
+            for (unsigned g = 0; g < (unsigned)in.G && ok; ++g)
+                ok = (unsigned)(((unsigned long long)g * in.divN_mul) >> in.divN_shift) == g / (unsigned)N[k];
+            if (ok) break;
+        }
+        const size_t moff = (b->mats.size() + 15) & ~(size_t)15;
+        const size_t msize = np == 4 ? sizeof(OpMats<double, 4>) : np == 6 ? sizeof(OpMats<double, 6>)
+                           : np == 8 ? sizeof(OpMats<double, 8>) : sizeof(OpMats<double, 10>);
+        b->mats.resize(moff + msize);
+        if (np == 4) fill_opmats<4>(b->mats.data() + moff, mats.data());
+        else if (np == 6) fill_opmats<6>(b->mats.data() + moff, mats.data());
+        else if (np == 8) fill_opmats<8>(b->mats.data() + moff, mats.data());
+        else fill_opmats<10>(b->mats.data() + moff, mats.data());
+        in.mats_off = (unsigned)moff;
+        b->inst.push_back(in);
+        b->row_start.push_back((int)b->rows.size());
+        for (int c = 0; c < 2; ++c)
+            for (int gy = 0; gy < in.G; ++gy) b->rows.push_back({k, c, gy});
+        off += 2 * (size_t)in.G * in.G;
+        loff += (size_t)in.nelem * 2 * np * np;
+        nel += in.nelem;
+        if (off > 2147483647u) {
+            delete b;
+            return fail(SEM_ERR_ARG, "batch too large: more than 2^31-1 unknowns");
+        }
+    }
+    b->row_start.push_back((int)b->rows.size());
+    b->J.assign(count, 0.0);
+    sem_ctx* h = new sem_ctx();
+    h->batch = b;
+    h->dim = 2;
+    h->precision = SEM_PREC_FP64;
+    h->ckpt_mode = common ? common->ckpt_mode : SEM_CKPT_AUTO;
+    h->ckpt_slots = common ? common->ckpt_slots : 0;
+    h->ckpt_budget = common ? common->ckpt_budget_bytes : 0;
+    h->ndof = off;
+    h->lvec_elems = loff;
+    h->nelem = (int)nel;
+    h->E = b->inst[0].E;
+    h->N = b->inst[0].N;
+    h->np = b->inst[0].NP;
+    h->G = b->inst[0].G;
+    h->L = Lbox;
+    h->h = Lbox / h->E;
+    *out = h;
+    g_err.clear();
+    return SEM_OK;
+}
+
+int sem_batch_count(sem_t h) { return (h && h->batch) ? h->batch->count : 0; }
+
+int sem_batch_layout(sem_t h, int k, size_t* offset, size_t* ndof) {
+    if (!h || !h->batch || k < 0 || k >= h->batch->count || !offset || !ndof)
+        return fail(SEM_ERR_ARG, "batch handle, 0 <= k < count and non-null outputs");
+    const BatchInst& in = h->batch->inst[k];
+    *offset = in.off;
+    *ndof = 2 * (size_t)in.G * in.G;
+    return SEM_OK;
+}
+
+int sem_batch_coords(sem_t h, int k, double* x) {
+    if (!h || !h->batch || k < 0 || k >= h->batch->count || !x)
+        return fail(SEM_ERR_ARG, "batch handle, 0 <= k < count and a non-null output");
+    const BatchInst& in = h->batch->inst[k];
+    std::vector<double> xi, w;
+    semh::gll(in.N, xi, w);
+    const double hk = h->L / in.E;
+    for (int g = 0; g < in.G; ++g) x[g] = (g / in.N) * hk + (xi[g % in.N] + 1.0) * hk / 2.0;
+    return SEM_OK;
+}
+
+int sem_batch_autotune(sem_t h, double* ms4, int* threads, void* stream) {
+    if (!h || !h->batch) return fail(SEM_ERR_ARG, "batch handle required");
+    SEM_TRY(ensure_workspace(h));
+    SEM_TRY(batch_tune(h, (cudaStream_t)stream));
+    if (ms4)
+        for (int i = 0; i < 4; ++i) ms4[i] = h->batch->tune_ms[i];
+    if (threads) *threads = h->batch->threads;
+    return SEM_OK;
+}
+
+int sem_batch_objective_grad(sem_t h, int scheme, double dt, int nsteps, const double* u0, const double* uo,
+                             double* J_host, double* grad, void* stream) {
+    if (!h || !h->batch || !J_host) return fail(SEM_ERR_ARG, "batch handle and J_host required");
+    double Jtot = 0.0;
+    SEM_TRY(sem_objective_grad(h, scheme, dt, nsteps, u0, uo, &Jtot, grad, stream));
+    SEM_CK(cudaMemcpy(J_host, h->batch->d_J, sizeof(double) * h->batch->count, cudaMemcpyDeviceToHost));
     return SEM_OK;
 }
 

@@ -30,6 +30,7 @@ struct Epi {
     double beta[3][4];
     int nout, nsrc;
     unsigned* nonfinite;  // set to 1 if any output is NaN/Inf (may be null)
+    int f2;               // FP32 form: out/src are float-pair planes (lo plane at +ndof floats)
     double alpha_k[3][4]; // filled by launch_assemble
 };
 
@@ -69,6 +70,55 @@ struct HandleView {
 };
 int handle_view(struct ::sem_ctx* h, HandleView* v);
 void set_error(const char* msg);
+
+// --------------------------------------------------------------- batches
+// Many independent 2D instances of uneven E and N packed into one vector:
+// instance k owns unknowns [off, off + 2 G^2) in the single-instance layout.
+struct BatchInst {
+    int E, N, NP, G, nelem;
+    unsigned off;             // first unknown of the instance in the packed vector
+    unsigned GD;              // G^2
+    unsigned long long loff;  // first value of the instance in the element-local buffer
+    unsigned mats_off;        // byte offset of its OpMats<double, NP> in the matrix table
+    unsigned divN_mul;        // g / N == (g * divN_mul) >> divN_shift on 0 <= g < G
+    int divN_shift;
+    double mw[16];            // assembled 1D GLL weights by position (misfit mass)
+    double scale;             // (h/2)^2
+};
+struct WorkItem { int inst, e0, ne, np; };  // ne elements of one instance from element e0
+struct RowInfo { int inst, c, gy; };        // one grid row of one component
+
+struct BatchDev {
+    const BatchInst* inst;
+    const WorkItem* items;
+    int nitems;
+    const RowInfo* rows;
+    int nrows;
+    const unsigned char* mats;
+};
+
+// the batched element kernel: one persistent launch over all work items
+cudaError_t launch_batch_elem(const BatchDev& b, int op, const double* u, const double* w, double* lvec,
+                              int threads, int blocks, size_t smem, cudaStream_t s);
+size_t batch_elem_smem(int threads, int op);   // shared memory for the largest supported order
+bool batch_np_supported(int np);
+cudaError_t launch_batch_assemble(const BatchDev& b, const double* lvec, int scale_mult, const Epi& ep,
+                                  cudaStream_t s);
+// per-instance misfit: J[k] = 1/2 (u - uo)^T M (u - uo) over instance k, total in *Jtot
+cudaError_t launch_batch_objective(const BatchDev& b, const double* u, const double* uo, double* lam,
+                                   double* row_partials, const int* row_start, int count, double* J,
+                                   double* Jtot, cudaStream_t s);
+template <int NP>
+void fill_opmats(void* dst, const double* mats);   // even/odd split of the 4 element matrices (host)
+
+// FP32-form conversions at the API boundary (integer instructions for the split).
+cudaError_t launch_f64_to_f2(const double* in, float* out, size_t n, cudaStream_t s);
+cudaError_t launch_f2_to_f64(const float* in, double* out, size_t n, cudaStream_t s);
+// misfit with a float-pair state u and float-pair output lam (FP64 arithmetic)
+cudaError_t launch_objective_f2(const float* u, const double* uo, float* lam, double* partials, int nblocks,
+                                const ObjArgs& a, cudaStream_t s);
+// out <- alpha * in for float-pair vectors (pair arithmetic)
+cudaError_t launch_scale_f2(float* out, const float* in, double alpha, size_t n, cudaStream_t s);
 
 // out <- alpha * in  (n doubles)
 cudaError_t launch_scale(double* out, const double* in, double alpha, size_t n, cudaStream_t s);

@@ -10,6 +10,9 @@
 // per axis), so the result is bitwise reproducible run to run.
 #include <math.h>
 
+#include <type_traits>
+
+#include "df64.cuh"
 #include "sem_internal.h"
 
 namespace semk {
@@ -26,91 +29,179 @@ __device__ __forceinline__ bool nonfinite_bits(double v) {
 // The launch grid is (ceil(G / 128), G, d) for d = 2 and (ceil(G / 128), G, d G)
 // for d = 3, so a thread finds its node without integer division (32-bit
 // division and modulo issue conversion instructions on the FP64 pipe); the
-// element index along an axis is a multiply-shift checked on the host.
-template <typename T, int D>
+// element index along an axis is a multiply-shift checked on the host.  The y
+// and z coordinates are uniform over a block, so only the x sharing differs
+// between the lanes of a warp: each thread issues the FP64 adds its node needs
+// and no predicated-off ones.  The numbers of epilogue outputs and sources are
+// template parameters for the same reason.
+template <typename T, int D, int NOUT, int NSRC>
 __global__ void __launch_bounds__(128) assemble_kernel(const T* __restrict__ lvec, const AsmArgs a,
                                                        const Epi ep) {
-    int g[3];
-    int c;
-    g[0] = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g[0] >= a.G) return;
-    if (D == 1) {
-        c = 0;
-    } else if (D == 2) {
-        g[1] = blockIdx.y;
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gx >= a.G) return;
+    int gy = 0, gz = 0, c = 0;
+    if (D == 2) {
+        gy = blockIdx.y;
         c = blockIdx.z;
-    } else {
-        g[1] = blockIdx.y;
+    } else if (D == 3) {
+        gy = blockIdx.y;
         c = blockIdx.z / a.G;          // once per block: blockIdx.z < 3G
-        g[2] = blockIdx.z - c * a.G;
+        gz = blockIdx.z - c * a.G;
     }
-    unsigned idx = c * a.GD;
-    {
-        unsigned st = 1;
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-            idx += g[d] * st;
-            st *= a.G;
-        }
+    const unsigned idx = c * a.GD + ((unsigned)gz * a.G + gy) * a.G + gx;
+    const unsigned npd = D == 1 ? a.NP : (D == 2 ? a.NP * a.NP : a.NP * a.NP * a.NP);
+    auto split = [&](int g, int& e0, int& i0, int& e1) {
+        e0 = (int)(((unsigned)g * a.divN_mul) >> a.divN_shift);
+        i0 = g - e0 * a.N;
+        e1 = e0 == 0 ? a.E - 1 : e0 - 1;
+        return i0 == 0;
+    };
+    int ex0, ix0, ex1, ey0 = 0, iy0 = 0, ey1 = 0, ez0 = 0, iz0 = 0, ez1 = 0;
+    const bool shx = split(gx, ex0, ix0, ex1);
+    const bool shy = D >= 2 ? split(gy, ey0, iy0, ey1) : false;
+    const bool shz = D >= 3 ? split(gz, ez0, iz0, ez1) : false;
+    const int nsh = (int)shx + (int)shy + (int)shz;
+    // value of element (ex, ey, ez) at local node (ix, iy, iz)
+    auto L = [&](int ex, int ix, int ey, int iy, int ez, int iz) -> T {
+        const unsigned el = ((unsigned)ez * a.E + ey) * a.E + ex;
+        const unsigned node = ((unsigned)iz * a.NP + iy) * a.NP + ix;
+        return lvec[((size_t)el * D + c) * npd + node];
+    };
+    // fixed summation order: x pairs first, then y, then z
+    using Acc = typename std::conditional<sizeof(T) == 8, double, float>::type;
+    Acc sum = L(ex0, ix0, ey0, iy0, ez0, iz0);
+    if (shx) sum += L(ex1, a.N, ey0, iy0, ez0, iz0);
+    if (D >= 2 && shy) {
+        Acc t = L(ex0, ix0, ey1, a.N, ez0, iz0);
+        if (shx) t += L(ex1, a.N, ey1, a.N, ez0, iz0);
+        sum += t;
     }
-    int npd = a.NP;
-    if (D >= 2) npd *= a.NP;
-    if (D >= 3) npd *= a.NP;
-    int e0[3], e1[3], i0[3];
-    int shmask = 0, nsh = 0;
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-        e0[d] = (int)(((unsigned)g[d] * a.divN_mul) >> a.divN_shift);
-        i0[d] = g[d] - e0[d] * a.N;
-        e1[d] = e0[d] == 0 ? a.E - 1 : e0[d] - 1;
-        if (i0[d] == 0) {
-            shmask |= 1 << d;
-            ++nsh;
+    if (D >= 3 && shz) {
+        Acc t = L(ex0, ix0, ey0, iy0, ez1, a.N);
+        if (shx) t += L(ex1, a.N, ey0, iy0, ez1, a.N);
+        if (shy) {
+            Acc t2 = L(ex0, ix0, ey1, a.N, ez1, a.N);
+            if (shx) t2 += L(ex1, a.N, ey1, a.N, ez1, a.N);
+            t += t2;
         }
+        sum += t;
     }
-    // contributions in a fixed order: combo = bit pattern of the "left neighbour" choices
-    T sumT = (T)0;
-    double sum = 0.0;
-    bool first = true;
-#pragma unroll
-    for (int combo = 0; combo < (1 << D); ++combo) {
-        if (combo & ~shmask) continue;
-        unsigned el = 0, node = 0;
-#pragma unroll
-        for (int d = D - 1; d >= 0; --d) {
-            const bool bit = (combo >> d) & 1;
-            el = el * a.E + (bit ? e1[d] : e0[d]);
-            node = node * a.NP + (bit ? a.N : i0[d]);
-        }
-        const T v = lvec[((size_t)el * D + c) * (size_t)npd + node];
-        if constexpr (sizeof(T) == 8) {
-            sum = first ? (double)v : sum + (double)v;
-        } else {
-            sumT = first ? v : sumT + v;
-        }
-        first = false;
-    }
-    if constexpr (sizeof(T) != 8) sum = (double)sumT;
+    const double sumd = (double)sum;
     // read every source before writing any output: an output may be a source (in place)
-    double sv[4];
+    double sv[NSRC > 0 ? NSRC : 1];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) sv[m] = m < ep.nsrc ? ep.src[m][idx] : 0.0;
-    double ov[3];
+    for (int m = 0; m < NSRC; ++m) sv[m] = ep.src[m][idx];
+    double ov[NOUT];
     bool bad = false;
 #pragma unroll
-    for (int o = 0; o < 3; ++o) {
-        if (o >= ep.nout) break;
-        double v = ep.alpha_k[o][nsh] * sum;
+    for (int o = 0; o < NOUT; ++o) {
+        double v = ep.alpha_k[o][nsh] * sumd;
 #pragma unroll
-        for (int m = 0; m < 4; ++m)
-            if (m < ep.nsrc) v = fma(ep.beta[o][m], sv[m], v);
+        for (int m = 0; m < NSRC; ++m) v = fma(ep.beta[o][m], sv[m], v);
         ov[o] = v;
         bad |= nonfinite_bits(v);
     }
 #pragma unroll
-    for (int o = 0; o < 3; ++o)
-        if (o < ep.nout) ep.out[o][idx] = ov[o];
+    for (int o = 0; o < NOUT; ++o) ep.out[o][idx] = ov[o];
     if (bad && ep.nonfinite) atomicOr(ep.nonfinite, 1u);
+}
+
+// FP32 form.  The element contributions are summed in FP32 (same order as
+// above); the epilogue either widens the sum to a caller's double (plain apply,
+// F2 = false, no sources) or runs in float-pair arithmetic on float-pair planes:
+// out = alpha a + sum_m beta_m src_m with alpha, beta as float pairs.
+struct EpiF2 {
+    float* out[3];
+    df alpha_k[3][4];
+    const float* src[4];
+    df beta[3][4];
+    double* out_f64;
+    unsigned plane;
+    unsigned* nonfinite;
+};
+
+template <int D, int NOUT, int NSRC, bool F2>
+__global__ void __launch_bounds__(128) assemble_f32_kernel(const float* __restrict__ lvec, const AsmArgs a,
+                                                           const EpiF2 ep) {
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (gx >= a.G) return;
+    int gy = 0, gz = 0, c = 0;
+    if (D == 2) {
+        gy = blockIdx.y;
+        c = blockIdx.z;
+    } else if (D == 3) {
+        gy = blockIdx.y;
+        c = blockIdx.z / a.G;
+        gz = blockIdx.z - c * a.G;
+    }
+    const unsigned idx = c * a.GD + ((unsigned)gz * a.G + gy) * a.G + gx;
+    const unsigned npd = D == 1 ? a.NP : (D == 2 ? a.NP * a.NP : a.NP * a.NP * a.NP);
+    auto split = [&](int g, int& e0, int& i0, int& e1) {
+        e0 = (int)(((unsigned)g * a.divN_mul) >> a.divN_shift);
+        i0 = g - e0 * a.N;
+        e1 = e0 == 0 ? a.E - 1 : e0 - 1;
+        return i0 == 0;
+    };
+    int ex0, ix0, ex1, ey0 = 0, iy0 = 0, ey1 = 0, ez0 = 0, iz0 = 0, ez1 = 0;
+    const bool shx = split(gx, ex0, ix0, ex1);
+    const bool shy = D >= 2 ? split(gy, ey0, iy0, ey1) : false;
+    const bool shz = D >= 3 ? split(gz, ez0, iz0, ez1) : false;
+    const int nsh = (int)shx + (int)shy + (int)shz;
+    auto L = [&](int ex, int ix, int ey, int iy, int ez, int iz) -> float {
+        const unsigned el = ((unsigned)ez * a.E + ey) * a.E + ex;
+        const unsigned node = ((unsigned)iz * a.NP + iy) * a.NP + ix;
+        return lvec[((size_t)el * D + c) * npd + node];
+    };
+    float sum = L(ex0, ix0, ey0, iy0, ez0, iz0);
+    if (shx) sum += L(ex1, a.N, ey0, iy0, ez0, iz0);
+    if (D >= 2 && shy) {
+        float t = L(ex0, ix0, ey1, a.N, ez0, iz0);
+        if (shx) t += L(ex1, a.N, ey1, a.N, ez0, iz0);
+        sum += t;
+    }
+    if (D >= 3 && shz) {
+        float t = L(ex0, ix0, ey0, iy0, ez1, a.N);
+        if (shx) t += L(ex1, a.N, ey0, iy0, ez1, a.N);
+        if (shy) {
+            float t2 = L(ex0, ix0, ey1, a.N, ez1, a.N);
+            if (shx) t2 += L(ex1, a.N, ey1, a.N, ez1, a.N);
+            t += t2;
+        }
+        sum += t;
+    }
+    if constexpr (!F2) {
+        // plain apply: alpha = 1, no sources; 1/k (F and J only) is an exact power of two
+        const float v = a.scale_mult ? sum * (nsh == 0 ? 1.f : (nsh == 1 ? 0.5f : (nsh == 2 ? 0.25f : 0.125f))) : sum;
+        ep.out_f64[idx] = widen_bits(v);
+        if (nonfinite_f(v) && ep.nonfinite) atomicOr(ep.nonfinite, 1u);
+    } else {
+        df sv[NSRC > 0 ? NSRC : 1];
+#pragma unroll
+        for (int m = 0; m < NSRC; ++m) sv[m] = {ep.src[m][idx], ep.src[m][ep.plane + idx]};
+        df ov[NOUT];
+        bool bad = false;
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) {
+            df v = df_mul_f(ep.alpha_k[o][nsh], sum);
+#pragma unroll
+            for (int m = 0; m < NSRC; ++m) v = df_add(v, df_mul(ep.beta[o][m], sv[m]));
+            ov[o] = v;
+            bad |= nonfinite_f(v.hi);
+        }
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) {
+            ep.out[o][idx] = ov[o].hi;
+            ep.out[o][ep.plane + idx] = ov[o].lo;
+        }
+        if (bad && ep.nonfinite) atomicOr(ep.nonfinite, 1u);
+    }
+}
+
+static df df_of(double x) {
+    df r;
+    r.hi = (float)x;
+    r.lo = (float)(x - (double)r.hi);
+    return r;
 }
 
 // Multiply-shift for g / N on 0 <= g < G, verified exhaustively (G <= 65535).
@@ -151,17 +242,69 @@ cudaError_t launch_assemble(bool lvec_fp32, const void* lvec, const AsmArgs& a_i
         grid.y = a.G;
         grid.z = 3 * a.G;
     }
-#define SEMK_ASM(T, D) assemble_kernel<T, D><<<grid, threads, 0, s>>>((const T*)lvec, a, ep)
-    if (lvec_fp32) {
-        if (a.D == 1) SEMK_ASM(float, 1);
-        else if (a.D == 2) SEMK_ASM(float, 2);
-        else SEMK_ASM(float, 3);
-    } else {
-        if (a.D == 1) SEMK_ASM(double, 1);
-        else if (a.D == 2) SEMK_ASM(double, 2);
-        else SEMK_ASM(double, 3);
+    if (ep.nout < 1 || ep.nout > 3 || ep.nsrc < 0 || ep.nsrc > 4) return cudaErrorInvalidValue;
+#define SEMK_ASM_NS(T, D, NO)                                                                          \
+    switch (ep.nsrc) {                                                                                 \
+        case 0: assemble_kernel<T, D, NO, 0><<<grid, threads, 0, s>>>((const T*)lvec, a, ep); break; \
+        case 1: assemble_kernel<T, D, NO, 1><<<grid, threads, 0, s>>>((const T*)lvec, a, ep); break; \
+        case 2: assemble_kernel<T, D, NO, 2><<<grid, threads, 0, s>>>((const T*)lvec, a, ep); break; \
+        case 3: assemble_kernel<T, D, NO, 3><<<grid, threads, 0, s>>>((const T*)lvec, a, ep); break; \
+        default: assemble_kernel<T, D, NO, 4><<<grid, threads, 0, s>>>((const T*)lvec, a, ep); break; \
     }
-#undef SEMK_ASM
+#define SEMK_ASM_NO(T, D)                           \
+    switch (ep.nout) {                              \
+        case 1: SEMK_ASM_NS(T, D, 1) break;         \
+        case 2: SEMK_ASM_NS(T, D, 2) break;         \
+        default: SEMK_ASM_NS(T, D, 3) break;        \
+    }
+    if (lvec_fp32) {
+        if (!ep.f2) {
+            // plain apply of the FP32 form: alpha = 1, one double output, no sources
+            if (ep.nout != 1 || ep.nsrc != 0 || ep.alpha[0] != 1.0) return cudaErrorInvalidValue;
+            EpiF2 e2{};
+            e2.out_f64 = ep.out[0];
+            e2.nonfinite = ep.nonfinite;
+            if (a.D == 1) assemble_f32_kernel<1, 1, 0, false><<<grid, threads, 0, s>>>((const float*)lvec, a, e2);
+            else if (a.D == 2) assemble_f32_kernel<2, 1, 0, false><<<grid, threads, 0, s>>>((const float*)lvec, a, e2);
+            else assemble_f32_kernel<3, 1, 0, false><<<grid, threads, 0, s>>>((const float*)lvec, a, e2);
+            return cudaGetLastError();
+        }
+        EpiF2 e2{};
+        for (int o = 0; o < 3; ++o) {
+            e2.out[o] = (float*)ep.out[o];
+            for (int k = 0; k < 4; ++k) e2.alpha_k[o][k] = df_of(ep.alpha_k[o][k]);
+            for (int m = 0; m < 4; ++m) e2.beta[o][m] = df_of(ep.beta[o][m]);
+        }
+        for (int m = 0; m < 4; ++m) e2.src[m] = (const float*)ep.src[m];
+        e2.plane = a.ndof;
+        e2.nonfinite = ep.nonfinite;
+#define SEMK_F2_NS(D, NO)                                                                                 \
+    switch (ep.nsrc) {                                                                                    \
+        case 0: assemble_f32_kernel<D, NO, 0, true><<<grid, threads, 0, s>>>((const float*)lvec, a, e2); break; \
+        case 1: assemble_f32_kernel<D, NO, 1, true><<<grid, threads, 0, s>>>((const float*)lvec, a, e2); break; \
+        case 2: assemble_f32_kernel<D, NO, 2, true><<<grid, threads, 0, s>>>((const float*)lvec, a, e2); break; \
+        case 3: assemble_f32_kernel<D, NO, 3, true><<<grid, threads, 0, s>>>((const float*)lvec, a, e2); break; \
+        default: assemble_f32_kernel<D, NO, 4, true><<<grid, threads, 0, s>>>((const float*)lvec, a, e2); break; \
+    }
+#define SEMK_F2_NO(D)                         \
+    switch (ep.nout) {                        \
+        case 1: SEMK_F2_NS(D, 1) break;       \
+        case 2: SEMK_F2_NS(D, 2) break;       \
+        default: SEMK_F2_NS(D, 3) break;      \
+    }
+        if (a.D == 1) { SEMK_F2_NO(1) }
+        else if (a.D == 2) { SEMK_F2_NO(2) }
+        else { SEMK_F2_NO(3) }
+#undef SEMK_F2_NO
+#undef SEMK_F2_NS
+        return cudaGetLastError();
+    } else {
+        if (a.D == 1) { SEMK_ASM_NO(double, 1) }
+        else if (a.D == 2) { SEMK_ASM_NO(double, 2) }
+        else { SEMK_ASM_NO(double, 3) }
+    }
+#undef SEMK_ASM_NO
+#undef SEMK_ASM_NS
     return cudaGetLastError();
 }
 
@@ -256,6 +399,97 @@ cudaError_t launch_scale(double* out, const double* in, double alpha, size_t n, 
     size_t blocks = (n + 255) / 256;
     if (blocks > 65535u * 16u) blocks = 65535u * 16u;
     scale_kernel<<<(unsigned)blocks, 256, 0, s>>>(out, in, alpha, n);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ FP32 form
+__global__ void f64_to_f2_kernel(const double* __restrict__ in, float* __restrict__ out, size_t n) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        float hi, lo;
+        split_bits(in[i], hi, lo);
+        out[i] = hi;
+        out[n + i] = lo;
+    }
+}
+
+__global__ void f2_to_f64_kernel(const float* __restrict__ in, double* __restrict__ out, size_t n) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride)
+        out[i] = widen_bits(in[i]) + widen_bits(in[n + i]);
+}
+
+__global__ void scale_f2_kernel(float* __restrict__ out, const float* __restrict__ in, df alpha, size_t n) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const df v = df_mul(alpha, df{in[i], in[n + i]});
+        out[i] = v.hi;
+        out[n + i] = v.lo;
+    }
+}
+
+// J partial sums and lam = M (u - uo) for a float-pair state (FP64 arithmetic, once per gradient)
+__global__ void __launch_bounds__(OBJ_THREADS) objective_f2_kernel(const float* __restrict__ u,
+                                                                   const double* __restrict__ uo,
+                                                                   float* __restrict__ lam,
+                                                                   double* __restrict__ partials,
+                                                                   const ObjArgs a) {
+    __shared__ double ws[OBJ_THREADS / 32];
+    double acc = 0.0;
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned idx = blockIdx.x * blockDim.x + threadIdx.x; idx < a.ndof; idx += stride) {
+        unsigned r = idx % a.GD;
+        double m = a.scale;
+        for (int d = 0; d < a.D; ++d) {
+            const unsigned g = r % (unsigned)a.G;
+            r /= (unsigned)a.G;
+            m *= a.mw[g % (unsigned)a.N];
+        }
+        const double diff = (widen_bits(u[idx]) + widen_bits(u[a.ndof + idx])) - uo[idx];
+        const double l = m * diff;
+        float hi, lo;
+        split_bits(l, hi, lo);
+        lam[idx] = hi;
+        lam[a.ndof + idx] = lo;
+        acc = fma(diff, l, acc);
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < OBJ_THREADS / 32 ? ws[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) partials[blockIdx.x] = v;
+    }
+}
+
+static unsigned grid_for(size_t n) {
+    size_t blocks = (n + 255) / 256;
+    if (blocks > 152u * 64u) blocks = 152u * 64u;
+    return (unsigned)(blocks ? blocks : 1);
+}
+
+cudaError_t launch_f64_to_f2(const double* in, float* out, size_t n, cudaStream_t s) {
+    if (!n) return cudaSuccess;
+    f64_to_f2_kernel<<<grid_for(n), 256, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f2_to_f64(const float* in, double* out, size_t n, cudaStream_t s) {
+    if (!n) return cudaSuccess;
+    f2_to_f64_kernel<<<grid_for(n), 256, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_f2(float* out, const float* in, double alpha, size_t n, cudaStream_t s) {
+    if (!n) return cudaSuccess;
+    scale_f2_kernel<<<grid_for(n), 256, 0, s>>>(out, in, df_of(alpha), n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_objective_f2(const float* u, const double* uo, float* lam, double* partials, int nblocks,
+                                const ObjArgs& a, cudaStream_t s) {
+    objective_f2_kernel<<<nblocks, OBJ_THREADS, 0, s>>>(u, uo, lam, partials, a);
     return cudaGetLastError();
 }
 

@@ -30,6 +30,12 @@ def batch_seeds(k):
     return 1000 + 2 * k, 1001 + 2 * k
 
 
+def batch_shapes(count=256, seed=4, E_choices=(8, 16, 24, 32, 48), N_choices=(5, 7, 9)):
+    """Seeded uneven instance sizes: (E per side, order N) for each of `count` instances."""
+    rng = np.random.default_rng(seed)
+    return [int(e) for e in rng.choice(E_choices, count)], [int(n) for n in rng.choice(N_choices, count)]
+
+
 def field_1d(x, seed):
     rng = np.random.default_rng(seed)
     a = rng.standard_normal(4)

@@ -95,3 +95,20 @@ def test_checkpoint_planner_is_dp_optimal(L):
     assert ckpt_plan(1000, 19) == optimal_advances(1000, 19)
     with pytest.raises(Exception):
         ckpt_plan(0, 3)
+
+
+def test_batch_create_validates_and_lays_out_packed_vectors(L):
+    from paper_1806_01422_gb300 import SemBatch
+    b = SemBatch([2, 3, 4], [5, 7, 9], [1e-3, 1e-3, 1e-3], device="cpu")
+    offs = [o for o, _ in b.layout]
+    sizes = [n for _, n in b.layout]
+    assert sizes == [2 * (2 * 5) ** 2, 2 * (3 * 7) ** 2, 2 * (4 * 9) ** 2]
+    assert offs == [0, sizes[0], sizes[0] + sizes[1]]
+    assert b.ndof == sum(sizes)
+    assert np.max(np.abs(b.coords(1) - Grid(2, 3, 7, 0.0).coords())) < 1e-15
+    for bad in (([2], [4], [1e-3]), ([0], [5], [1e-3]), ([2], [5], [-1.0])):
+        with pytest.raises(L.SemError):
+            SemBatch(*bad, device="cpu")
+    Ea = (ctypes.c_int * 1)(2)
+    h = ctypes.c_void_p()
+    assert L.lib().sem_batch_create(0, Ea, Ea, (ctypes.c_double * 1)(0.1), None, ctypes.byref(h)) == L.SEM_ERR_ARG
