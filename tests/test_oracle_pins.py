@@ -326,3 +326,57 @@ def test_checkpointed_gradient_equals_store_all_bitwise(nsteps, slots):
     got, count = checkpointed_gradient_lam0(g.rhs, g.jacT, u0, lamT, 1e-2, nsteps, "rk4", slots)
     assert np.array_equal(got, ref)
     assert count == optimal_advances(nsteps, slots)
+
+
+# ------------------------------------------------ Crank-Nicolson (Sec. 6.3, implicit scheme)
+from oracle import cn as ocn
+
+
+def test_cn_step_is_the_1_1_pade_approximant_on_linear_problems():
+    """For F(u) = A u one CN step is (I - dt A/2)^-1 (I + dt A/2) u, and its adjoint the transpose."""
+    rng = np.random.default_rng(21)
+    A = rng.standard_normal((7, 7))
+    dt = 0.2
+    u = rng.standard_normal(7)
+    un, _ = ocn.cn_step(lambda y: A @ y, lambda y, w: A @ w, u, dt)
+    R = np.linalg.solve(np.eye(7) - 0.5 * dt * A, np.eye(7) + 0.5 * dt * A)
+    assert np.max(np.abs(un - R @ u)) < 1e-13 * np.max(np.abs(R @ u))
+    lam = rng.standard_normal(7)
+    back = ocn.cn_adjoint(lambda y: A.T, [u, un], lam, dt)
+    assert np.max(np.abs(back - R.T @ lam)) < 1e-13 * np.max(np.abs(R.T @ lam))
+
+
+def test_cn_step_satisfies_its_residual_and_is_second_order():
+    g = Grid(1, 16, 9, 0.05, L=4.0)
+    x = g.coords()
+
+    def exact(t):
+        e = np.exp(-0.05 * t * np.pi ** 2)
+        return (2 * 0.05 * np.pi * np.sin(np.pi * x) * e / (2 + e * np.cos(np.pi * x)))[None]
+
+    errs = []
+    for steps in (10, 20):
+        uT, traj = ocn.cn_forward(g.rhs, g.jac, exact(0.0), 0.4 / steps, steps)
+        errs.append(np.max(np.abs(uT - exact(0.4))))
+        u0, u1 = traj[0], traj[1]
+        R = u1 - u0 - 0.5 * (0.4 / steps) * (g.rhs(u0) + g.rhs(u1))
+        assert np.max(np.abs(R)) < 1e-14
+    assert 3.0 < errs[0] / errs[1] < 5.0        # second order in time
+
+
+def test_cn_tangent_adjoint_duality_and_gradient():
+    g = Grid(2, 2, 3, 0.02)
+    rng = np.random.default_rng(22)
+    u0, du0, uo = 0.3 * rng.standard_normal((3, 2) + g.global_shape())
+    dt, steps = 5e-3, 4
+    uN, traj = ocn.cn_forward(g.rhs, g.jac, u0, dt, steps)
+    Jd = lambda u: ocn.assembled_jacobian(g.jac, u)
+    lamN = rng.standard_normal(u0.shape)
+    duN = ocn.cn_tangent(Jd, traj, du0, dt)
+    lam0 = ocn.cn_adjoint(lambda u: Jd(u).T, traj, lamN, dt)
+    assert abs(np.sum(lamN * duN) - np.sum(lam0 * du0)) < 1e-11 * np.linalg.norm(lamN) * np.linalg.norm(duN)
+    J0, grad, _ = ocn.cn_objective_and_gradient(g, u0, uo, dt, steps)
+    eps = 1e-5
+    fd = (ocn.cn_objective_and_gradient(g, u0 + eps * du0, uo, dt, steps)[0]
+          - ocn.cn_objective_and_gradient(g, u0 - eps * du0, uo, dt, steps)[0]) / (2 * eps)
+    assert abs(fd - np.sum(grad * du0)) < 1e-7 * abs(fd)
