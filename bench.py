@@ -44,6 +44,16 @@ WORKLOADS = {
                        "one persistent launch per operator pass, every step's state stored (stages recomputed); one "
                        "batched gradient evaluation per step (256 instance gradients)",
                   data="synthetic: per instance k seeded 16-mode Fourier fields (seeds 1000+2k, 1001+2k)"),
+    "3d15": dict(dim=3, E=16, N=15, nu=2e-4, scheme="rk4", dt=2e-4, nsteps=400, ckpt="states", slots=0,
+                 desc="3D vector viscous Burgers, periodic [0,1]^3, 16^3 hexes, N=15 (41,472,000 unknowns), "
+                      "nu=2e-4, RK4 dt=2e-4 x 400 steps, every step's state stored (stages recomputed)",
+                 data="synthetic: seeded random-phase fields, spectrum ~k^-5/3 cut at |k| = 16, max|u0| = 1"),
+    "2dcn": dict(dim=2, E=64, N=7, nu=1e-3, scheme="cn", dt=2e-3, nsteps=200, ckpt="states", slots=0,
+                 desc="2D vector viscous Burgers, periodic [0,1]^2, 64x64 quads, N=7 (401,408 unknowns), "
+                      "nu=1e-3, Crank-Nicolson dt=2e-3 x 200 steps (Newton + GMRES(30) to 1e-12 per step), "
+                      "every state stored; one gradient evaluation per step",
+                 data="synthetic: seeded 16-mode Fourier fields (|k|_inf <= 8, amplitude ~|k|^-2, max|u0| = 1) "
+                      "for u0 (seed 1) and u_obs (seed 2)"),
     "1d": dict(dim=1, E=16, N=7, nu=0.01, scheme="rk4", dt=1e-3, nsteps=500, ckpt="stages", slots=0,
                desc="1D viscous Burgers, periodic [0,2pi), 16 elements, N=7 (112 unknowns), nu=0.01, "
                     "RK4 dt=1e-3 x 500 steps",
@@ -58,14 +68,22 @@ PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 # DRAM traffic per launch (bytes) of the dominant kernel from one ncu capture,
 # valid only while the kernel sources hash to the recorded value.
-TRAFFIC = {}
+TRAFFIC = {
+    "jact2_kernel<double,8>@2d@fp64": {
+        "bytes": 6477312 + 0, "src": "e1753eeccab48628",
+        "capture": "dram__bytes_read.sum + dram__bytes_write.sum of one jact2 launch at 64x64 quads, N=7 "
+                   "(ncu --set full; profiles/rhs2_jact2_assemble_2d_fp64_E64_N7.md)"},
+}
 
-KERNEL_SOURCES = ["op_kernels.cuh", "op_elem.cuh", "op_launch.cuh", "vec_kernels.cu"]
+# sources of the element kernels (rhs*, jac*, jact*) and of the assembly kernels
+KERNEL_SOURCES = {"elem": ["op_kernels.cuh", "op_elem.cuh", "op_launch.cuh", "df64.cuh", "op_d1.cu", "op_d2.cu",
+                           "op_d3.cu"],
+                  "assemble": ["vec_kernels.cu", "df64.cuh"]}
 
 
-def kernel_src_hash():
+def kernel_src_hash(family):
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[family]:
         with open(os.path.join(ROOT, "paper_1806_01422_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -167,6 +185,10 @@ def run_oracle_child(workload, rk_steps):
 def cpu_baseline(workload, target_s=15.0):
     """Oracle gradient evaluations/s from a bounded sample, one core, scaled to the full horizon."""
     w = WORKLOADS[workload]
+    if w["scheme"] == "cn":
+        return {"value": None, "unit": "gradient evals/s", "cores": 1, "kind": "oracle",
+                "sample": "none: the oracle's Crank-Nicolson solves assemble dense Jacobians, which do not fit "
+                          "at %s" % w["desc"].split(", ")[2]}
     probe = run_oracle_child(workload, 2)
     per_step = max(probe["seconds"] / 2, 1e-6)
     n = int(max(2, min(w["nsteps"], target_s / per_step)))
@@ -218,6 +240,9 @@ def reference_arm(args, world, rank):
     if rank != 0:
         return None
     w = WORKLOADS[args.workload]
+    if w["scheme"] == "cn":
+        return {"impl": "reference", "unavailable": "the oracle's Crank-Nicolson solves assemble dense Jacobians, "
+                                                    "which do not fit at 401,408 unknowns"}
     n = args.oracle_rk_steps
     for _ in range(args.warmup):
         run_oracle_child(args.workload, n)
@@ -238,6 +263,7 @@ def reference_arm(args, world, rank):
 def gpu_arm(args, world, rank, local):
     import torch
     from paper_1806_01422_gb300 import Sem, inputs
+    from paper_1806_01422_gb300 import _lib as L
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -261,14 +287,33 @@ def gpu_arm(args, world, rank, local):
     u0, uo = u0_h.to(dev), uo_h.to(dev)
     grad = s.empty()
     nsteps, dt, scheme = w["nsteps"], w["dt"], w["scheme"]
+    if scheme == "cn":
+        args.no_graph = True    # the implicit solves synchronise with the host: never captured
 
     def step():
         return s.objective_grad(u0, uo, dt, nsteps, scheme, grad=grad)
 
-    for _ in range(args.warmup):
-        J, _ = step()
-    s.profile_read(reset=True)
+    # the gradient evaluation runs as one CUDA graph (recorded by the first warm-up call,
+    # with the sampled kernel-timing events inside it)
+    if not args.no_graph:
+        s.use_graph(True)
     s.profile(args.profile_every)
+    graph_note = None
+    try:
+        for _ in range(args.warmup):
+            J, _ = step()
+        s.profile_read(reset=True)
+    except L.SemError as e:
+        if args.no_graph:
+            raise
+        # timed event nodes inside the graph were refused: measure stream launches instead
+        graph_note = "graph replay with timed event nodes failed (%s); stream launches measured" % e
+        s.use_graph(False)
+        args.no_graph = True
+        s.profile(args.profile_every)
+        for _ in range(args.warmup):
+            J, _ = step()
+        s.profile_read(reset=True)
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -287,6 +332,13 @@ def gpu_arm(args, world, rank, local):
     value, tmax = job_value(elapsed, args.steps * units, world, dev)
     # element kernel + assembly per apply, plus misfit, partial sum and adjoint seed per step
     launches = args.steps * (2 * (st["forward_rhs"] + st["adjoint_rhs"] + st["adjoint_jacT"]) + 3)
+    if scheme == "cn":
+        # per Arnoldi step 5 two-kernel dot passes, 2 axpys and a scale; per GMRES solve a norm, a
+        # scale and the update; per Newton iteration the update and two norms
+        cs = s.solver_stats()
+        krylov = cs["forward_krylov"] + cs["adjoint_krylov"]
+        launches = args.steps * (2 * cs["applies"] + 13 * krylov + 4 * (cs["newton"] + nsteps)
+                                 + 5 * cs["newton"] + 3)
 
     # dominant kernel of the timed region and its roofline
     kinds = {k: v for k, v in prof.items() if v[1] > 0}
@@ -319,13 +371,24 @@ def gpu_arm(args, world, rank, local):
                                                          w["N"] + 1)}
     key = "%s@%s@%s" % (roof["kernel"], args.workload, args.precision)
     tr = TRAFFIC.get(key)
-    roof["traffic"] = tr["bytes"] if tr and tr["src"] == kernel_src_hash() else None
+    tr_ok = tr and tr["src"] == kernel_src_hash("assemble" if dom == "assemble" else "elem")
+    roof["traffic"] = tr["bytes"] if tr_ok else None
+    if tr_ok:
+        roof["traffic_source"] = tr["capture"]
+    if roof["bound"] == "alu":
+        roof["note"] = ("achieved counts the algorithmic flops of plain n-term contractions; the kernels split "
+                        "each contraction into even and odd halves (n^2/2 + n operations per line), so frac can "
+                        "exceed the fraction of FP pipe cycles ncu reports")
     roof["avg_launch_us"] = avg_s * 1e6
     roof["timed_launches"] = dom_n
-    roof["timing"] = "CUDA events around 1 in %d launches of each kernel kind, on the launching stream, " \
-                     "inside the timed region" % args.profile_every
+    roof["timing"] = "CUDA events around 1 in %d launches of each kernel kind, on the launching stream%s, " \
+                     "inside the timed region" % (args.profile_every,
+                                                  "" if args.no_graph else " (event nodes of the replayed graph)")
 
     unit = "instance gradient evals/s" if args.workload == "batch" else "gradient evals/s"
+    stages = {"rk4": 4, "ssprk3": 3, "euler": 1, "cn": 1}[scheme]
+    traj_gb = s.ndof * 8 / 1e9 * {"stages": nsteps * stages, "states": nsteps + (scheme == "cn"),
+                                  "binomial": w["slots"]}.get(w["ckpt"], nsteps)
     out = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": w["data"],
@@ -333,10 +396,13 @@ def gpu_arm(args, world, rank, local):
                       "instances": units,
                       "scheme": scheme, "dt": dt, "rk_steps": nsteps, "trajectory": w["ckpt"],
                       "precision": args.precision, "parallelism": "replicas" if world > 1 else "single GPU",
-                      "l2": "inputs larger than L2: every step writes and re-reads the stored stage trajectory "
-                            "(%.1f GB)" % (nsteps * 3 * s.ndof * 8 / 1e9 if w["ckpt"] == "stages" else 0.0)},
+                      "l2": "inputs larger than L2: every step writes and re-reads the stored trajectory "
+                            "(%.1f GB: %s)" % (traj_gb, w["ckpt"])},
            "roofline": roof, "gpu_launches": launches, "clocks": clk.summary(), "J": J,
+           "execution": graph_note or ("stream launches" if args.no_graph else "CUDA graph replay (sem_set_graph)"),
            "kernel_ms_per_step": {k: v[0] * args.profile_every / args.steps for k, v in prof.items()}}
+    if scheme == "cn":
+        out["solver"] = dict(s.solver_stats(), note="counters of the last gradient evaluation")
 
     if rank == 0 and not args.no_extras:
         out.update(extras(s, u0, uo, w, dev))
@@ -389,6 +455,42 @@ def extras(s, u0, uo, w, dev):
             "forward_ms": fwd, "adjoint_ms": adj, "adjoint_forward_ratio": adj / fwd}
 
 
+def order_sweep(precisions=("fp64", "fp32_bulk"), target=34e6, reps=10):
+    """Standalone F(u) and J^T v throughput over orders N at about `target` 3D unknowns."""
+    import torch
+    from paper_1806_01422_gb300 import Sem, inputs
+    rows = []
+    for prec in precisions:
+        for N in (3, 5, 7, 9, 11, 15):
+            if prec == "fp64" and N > 11:
+                continue
+            E = max(2, int(round((target / 3) ** (1 / 3) / N)))
+            s = Sem(3, E, N, 5e-4, precision=prec)
+            x = s.coords()
+            u = torch.from_numpy(inputs.field_3d(x, inputs.SEED_U0)).cuda()
+            v = torch.from_numpy(inputs.field_3d(x, inputs.SEED_UOBS)).cuda()
+            out = s.empty()
+            res = {}
+            for name, fn in (("F", lambda: s.rhs(u, out)), ("JT", lambda: s.jacT(u, v, out))):
+                for _ in range(3):
+                    fn()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                for _ in range(reps):
+                    fn()
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                res[name] = {"ms": ms, "gdofs": s.ndof / ms / 1e6}
+            rows.append({"precision": prec, "N": N, "E": E, "unknowns": s.ndof, **res,
+                         "JT_over_F": res["JT"]["ms"] / res["F"]["ms"]})
+            print(json.dumps(rows[-1]), flush=True)
+            del s, u, v, out
+            torch.cuda.empty_cache()
+    return rows
+
+
 def ops_once(dim, E, N, precision):
     """One F and one J^T apply (for ncu captures of the element and assembly kernels)."""
     import torch
@@ -419,14 +521,20 @@ def main():
                     help="override the workload's RK step count (profiling runs only; not a bench number)")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--profile-every", type=int, default=16, help="time one launch in this many per kernel kind")
+    ap.add_argument("--no-graph", action="store_true", help="launch on the stream instead of replaying a CUDA graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-sample", nargs=2, metavar=("WORKLOAD", "RK_STEPS"), help=argparse.SUPPRESS)
+    ap.add_argument("--order-sweep", action="store_true",
+                    help="standalone 3D F and J^T throughput over N in {3,5,7,9,11,15} at ~34M unknowns")
     ap.add_argument("--ops-once", nargs=4, metavar=("DIM", "E", "N", "PRECISION"),
                     help="profiling driver: one F and one J^T apply on the workload field of that size, no timing")
     args = ap.parse_args()
 
     if args.oracle_sample:
         print(json.dumps(oracle_sample(args.oracle_sample[0], int(args.oracle_sample[1]))))
+        return
+    if args.order_sweep:
+        order_sweep()
         return
     if args.ops_once:
         ops_once(int(args.ops_once[0]), int(args.ops_once[1]), int(args.ops_once[2]), args.ops_once[3])

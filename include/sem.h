@@ -54,6 +54,12 @@ typedef struct sem_ctx* sem_t;
 #define SEM_RK4      0  /* classic 4-stage, 4th order */
 #define SEM_SSPRK3   1  /* Shu-Osher SSP 3-stage, 3rd order */
 #define SEM_EULER    2  /* forward Euler (the case of Sec. 4.1) */
+/* implicit scheme */
+#define SEM_CN       3  /* Crank-Nicolson (Sec. 6.3): u_{n+1} - u_n = dt/2 (F(u_n) + F(u_{n+1})),
+                           Newton with matrix-free GMRES per step; FP64 single-instance
+                           handles only; stores every state u_0 .. u_N whatever the
+                           checkpoint mode; its adjoint solves with (I - dt/2 J^T)
+                           (see sem_set_solver) */
 
 /* arithmetic of the element kernels */
 #define SEM_PREC_FP64       0  /* everything in FP64 */
@@ -143,8 +149,10 @@ int sem_objective_grad(sem_t h, int scheme, double dt, int nsteps,
  * adjoint, backward sweep) into a CUDA graph on a private stream, after making
  * every allocation it needs, and each later call with the same scheme, dt,
  * nsteps and u0 / u_obs / grad pointers replays that graph on `stream`.  A
- * call with other arguments records a new graph.  Opt-in kernel timing is
- * suspended while recording.  enable = 0 releases the graph. */
+ * call with other arguments records a new graph.  With opt-in kernel timing
+ * (sem_profile) enabled while recording, the sampled launches' event pairs
+ * become nodes of the graph and every replay adds their times to the
+ * counters of sem_profile_read.  enable = 0 releases the graph. */
 int sem_set_graph(sem_t h, int enable);
 long long sem_graph_replays(sem_t h);   /* graph launches so far; -1 for a null handle */
 
@@ -159,6 +167,35 @@ int sem_ckpt_plan(int nsteps, int slots, long long* advances);
  * recomputation (stage taping and checkpoint replays), out3[2] = J^T applies in
  * the last adjoint sweep.  Host-only. */
 int sem_sweep_stats(sem_t h, long long* out3);
+
+/* Frozen advection: the linear problems of Sec. 6.1 (advection-diffusion with
+ * a given velocity).  With a != NULL (a device state, copied on `stream`), the
+ * time integrators of this handle (sem_rk_forward, sem_rk_adjoint and
+ * sem_objective_grad, every scheme) integrate the linear equation
+ *     du/dt = J(a) u = nu Lap u - (a . grad) u - (u . grad) a,
+ * the tangent of F at the fixed field a (eq. jacvec); for a constant field a
+ * this is u_t + a . grad u = nu Lap u, component by component.  Their adjoints
+ * use J(a)^T at every stage, so the forward sweep of an explicit scheme stores
+ * no trajectory.  sem_rhs, sem_jac_apply and sem_jacT_apply are unaffected.
+ * a == NULL returns the handle to Burgers.  Either call discards the recorded
+ * forward sweep and any recorded gradient graph. */
+int sem_set_advection(sem_t h, const double* a, void* stream);
+
+/* Settings of the SEM_CN solves (Sec. 6.3 names the scheme; the solver is this
+ * library's): Newton stops when |delta| <= newton_rtol max(|u_{n+1}|, 1) (2-norms);
+ * each linear system (I - dt/2 J(u)) x = b or (I - dt/2 J(u)^T) x = b runs
+ * restarted GMRES(krylov_m) from x = 0 until |b - A x| <= krylov_rtol |b|,
+ * failing with SEM_ERR_NONFINITE after krylov_maxit Arnoldi steps (likewise
+ * Newton after 30 iterations).  Defaults 1e-12, 1e-12, 30, 2000.
+ * 1 <= krylov_m <= 38.  Host-only apart from freeing the Krylov basis when
+ * krylov_m changes.  The solves synchronise their stream once per Arnoldi step,
+ * so with SEM_CN sem_objective_grad runs without a CUDA graph. */
+int sem_set_solver(sem_t h, double newton_rtol, double krylov_rtol, int krylov_m, int krylov_maxit);
+
+/* Counters of the last SEM_CN sweeps: out4[0] Newton iterations and out4[1]
+ * Arnoldi steps of the forward sweep, out4[2] Arnoldi steps of the adjoint
+ * sweep, out4[3] operator applies of both.  Host-only. */
+int sem_solver_stats(sem_t h, long long* out4);
 
 /* Opt-in kernel timing (no counterpart in the paper; used by the benchmarks).
  * With every = n > 0, one launch in n of each kind on this handle is bracketed

@@ -17,7 +17,7 @@ SEM_ERR_NONFINITE = -4
 SEM_ERR_STATE = -5
 SEM_ERR_CUDA = -6
 
-SEM_RK4, SEM_SSPRK3, SEM_EULER = 0, 1, 2
+SEM_RK4, SEM_SSPRK3, SEM_EULER, SEM_CN = 0, 1, 2, 3
 SEM_PREC_FP64, SEM_PREC_FP32_BULK = 0, 1
 SEM_CKPT_AUTO, SEM_CKPT_STAGES, SEM_CKPT_STATES, SEM_CKPT_BINOMIAL = 0, 1, 2, 3
 
@@ -54,6 +54,9 @@ _SIGS = {
     "sem_objective_grad": (_I, [_H, _I, _D, _I, _P, _P, ctypes.POINTER(_D), _P, _P]),
     "sem_ckpt_plan": (_I, [_I, _I, ctypes.POINTER(ctypes.c_longlong)]),
     "sem_sweep_stats": (_I, [_H, ctypes.POINTER(ctypes.c_longlong)]),
+    "sem_set_solver": (_I, [_H, _D, _D, _I, _I]),
+    "sem_set_advection": (_I, [_H, _P, _P]),
+    "sem_solver_stats": (_I, [_H, ctypes.POINTER(ctypes.c_longlong)]),
     "sem_profile": (_I, [_H, _I]),
     "sem_profile_read": (_I, [_H, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), _I]),
     "sem_rhs_noalloc": (_I, [_H, _P, _P, _P]),

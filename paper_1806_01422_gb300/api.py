@@ -12,7 +12,7 @@ import torch
 
 from . import _lib as L
 
-SCHEMES = {"rk4": L.SEM_RK4, "ssprk3": L.SEM_SSPRK3, "euler": L.SEM_EULER}
+SCHEMES = {"rk4": L.SEM_RK4, "ssprk3": L.SEM_SSPRK3, "euler": L.SEM_EULER, "cn": L.SEM_CN}
 PRECISIONS = {"fp64": L.SEM_PREC_FP64, "fp32_bulk": L.SEM_PREC_FP32_BULK}
 CKPT = {"auto": L.SEM_CKPT_AUTO, "stages": L.SEM_CKPT_STAGES, "states": L.SEM_CKPT_STATES,
         "binomial": L.SEM_CKPT_BINOMIAL}
@@ -150,6 +150,26 @@ class Sem:
         out = (ctypes.c_longlong * 3)()
         L.check(L.lib().sem_sweep_stats(self._h, out))
         return {"forward_rhs": out[0], "adjoint_rhs": out[1], "adjoint_jacT": out[2]}
+
+    def set_advection(self, a=None):
+        """Integrate du/dt = J(a) u (frozen advecting field a) instead of Burgers; None: back to Burgers."""
+        if a is None:
+            L.check(L.lib().sem_set_advection(self._h, None, _stream(self.device)))
+            self._frozen = None
+            return
+        a = self._dev(a, "a")
+        L.check(L.lib().sem_set_advection(self._h, self._p(a), _stream(self.device)))
+        self._frozen = a   # kept alive until the copy on the stream has run
+
+    def set_solver(self, newton_rtol=1e-12, krylov_rtol=1e-12, krylov_m=30, krylov_maxit=2000):
+        """Newton / GMRES settings of the Crank-Nicolson scheme (sem_set_solver)."""
+        L.check(L.lib().sem_set_solver(self._h, float(newton_rtol), float(krylov_rtol), int(krylov_m),
+                                       int(krylov_maxit)))
+
+    def solver_stats(self):
+        out = (ctypes.c_longlong * 4)()
+        L.check(L.lib().sem_solver_stats(self._h, out))
+        return {"newton": out[0], "forward_krylov": out[1], "adjoint_krylov": out[2], "applies": out[3]}
 
 
 class SemBatch(Sem):

@@ -38,7 +38,10 @@ int fail(int code, const char* fmt, ...) {
 #define SEM_CK(call)                                                                          \
     do {                                                                                      \
         cudaError_t e_ = (call);                                                              \
-        if (e_ != cudaSuccess) return fail(SEM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+        if (e_ != cudaSuccess) {                                                              \
+            cudaGetLastError(); /* a failed call must not be seen by the next launch check */ \
+            return fail(SEM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));               \
+        }                                                                                     \
     } while (0)
 
 #define SEM_TRY(expr)                  \
@@ -53,6 +56,15 @@ struct Tableau {
     double A[4][4];
     double b[4];
 };
+
+// Stage i depends only on k_{i-1} (A is subdiagonal): RK4, forward Euler.  The
+// sweeps then carry running sums instead of storing every stage derivative.
+bool subdiagonal(const Tableau& t) {
+    for (int i = 0; i < t.s; ++i)
+        for (int j = 0; j + 1 < i; ++j)
+            if (t.A[i][j] != 0.0) return false;
+    return true;
+}
 
 bool tableau_of(int scheme, Tableau& t) {
     std::memset(&t, 0, sizeof(t));
@@ -119,6 +131,7 @@ struct sem_ctx {
     double* scal = nullptr;      // [0] objective
     unsigned* flag = nullptr;    // non-finite flag
     double* vecs = nullptr;      // NVEC state-sized work vectors
+    double* frozen = nullptr;    // frozen advecting field a (a state; float pairs in the FP32 form) or null
     double* traj = nullptr;
     size_t traj_vectors = 0;
     // last forward sweep
@@ -141,6 +154,18 @@ struct sem_ctx {
     } graph_key{-1, 0, 0.0, nullptr, nullptr, nullptr};
     long long graph_replays = 0;
     int fixed_mode = -1, fixed_slots = 0;   // storage mode fixed before a graph recording
+    // kernel timing inside a recorded graph: the sampled launches' event pairs are
+    // nodes of the graph and are read after each replay
+    bool capturing = false;
+    std::vector<cudaEvent_t> gev_start, gev_stop;
+    std::vector<int> gev_kind;
+    // Crank-Nicolson: Newton / GMRES settings, Krylov workspace, counters
+    double newton_rtol = 1e-12, krylov_rtol = 1e-12;
+    int krylov_m = 30, krylov_maxit = 2000, newton_maxit = 30;
+    double* kbasis = nullptr;     // krylov_m + 2 vectors: the basis and a work vector
+    double* kpart = nullptr;      // multidot partials
+    double* kscal = nullptr;      // device scalars (2 KMAX)
+    long long cn_st[4] = {0, 0, 0, 0};  // Newton iterations, forward and adjoint Krylov steps, operator applies
     // opt-in kernel timing: event pairs per launch, drained when the pool fills
     int prof = 0;                 // 0: off; n: time one apply in n per kind
     long long prof_tick[4] = {0, 0, 0, 0};
@@ -154,6 +179,9 @@ struct sem_ctx {
 namespace {
 
 // work vector roles inside sem_ctx::vecs
+// internal storage mode of a linear (frozen-advection) sweep: nothing stored
+constexpr int MODE_LINEAR = 100;
+
 enum { V_K0 = 0, V_STAGE0 = 4, V_CUR0 = 7, V_CUR1 = 8, V_NU = 9, V_UN = 10, V_LAM = 11, NVEC = 12 };
 
 // FP32 form: every sweep-internal state is a pair of FP32 planes (hi at [0, ndof),
@@ -242,6 +270,18 @@ int prof_begin(sem_t h, int kind, cudaStream_t s, long long& slot) {
     slot = -1;
     if (!h->prof) return SEM_OK;
     if (h->prof_tick[kind]++ % h->prof != 0) return SEM_OK;
+    if (h->capturing) {
+        cudaEvent_t a, b;
+        SEM_CK(cudaEventCreate(&a));
+        SEM_CK(cudaEventCreate(&b));
+        h->gev_start.push_back(a);
+        h->gev_stop.push_back(b);
+        h->gev_kind.push_back(kind);
+        slot = -2 - (long long)(h->gev_start.size() - 1);
+        // an event recorded into a graph must be an external record node to be timed
+        SEM_CK(cudaEventRecordWithFlags(a, s, cudaEventRecordExternal));
+        return SEM_OK;
+    }
     if (h->ev_start.empty()) {
         h->ev_start.resize(PROF_POOL);
         h->ev_stop.resize(PROF_POOL);
@@ -260,7 +300,29 @@ int prof_begin(sem_t h, int kind, cudaStream_t s, long long& slot) {
 
 int prof_end(sem_t h, long long slot, cudaStream_t s) {
     if (slot >= 0) SEM_CK(cudaEventRecord(h->ev_stop[slot], s));
+    if (slot <= -2) SEM_CK(cudaEventRecordWithFlags(h->gev_stop[(size_t)(-2 - slot)], s, cudaEventRecordExternal));
     return SEM_OK;
+}
+
+// Accumulate the timed launches of the last graph replay (after its stream was synchronised).
+int prof_graph_accumulate(sem_t h) {
+    for (size_t i = 0; i < h->gev_start.size(); ++i) {
+        float ms = 0.f;
+        SEM_CK(cudaEventElapsedTime(&ms, h->gev_start[i], h->gev_stop[i]));
+        h->prof_ms[h->gev_kind[i]] += ms;
+        h->prof_n[h->gev_kind[i]] += 1;
+    }
+    return SEM_OK;
+}
+
+void prof_graph_release(sem_t h) {
+    for (size_t i = 0; i < h->gev_start.size(); ++i) {
+        cudaEventDestroy(h->gev_start[i]);
+        cudaEventDestroy(h->gev_stop[i]);
+    }
+    h->gev_start.clear();
+    h->gev_stop.clear();
+    h->gev_kind.clear();
 }
 
 // One operator apply: element kernel into the element-local buffer, then the
@@ -327,9 +389,52 @@ int add_src(Epi& ep, const double* p) {
 // Y_{i+1} goes to Y[i+1] (Y[0] is un); k_i to vec(V_K0 + i).  If unext is
 // non-null the last stage writes u_{n+1} = un + dt sum_i b_i k_i; otherwise the
 // step stops after Y_s (taping only: s-1 applies).
+// The stage derivative k = F(Y), or J(a) Y with a frozen advecting field a.
+int stage_rhs(sem_t h, const double* Y, const Epi& ep, cudaStream_t s) {
+    if (h->frozen) return apply(h, OP_JAC, h->frozen, Y, ep, s, f32(h));
+    return apply(h, OP_RHS, Y, nullptr, ep, s, f32(h));
+}
+
+// The linearisation point of the adjoint stage: Y itself, or the frozen field.
+const double* jac_point(sem_t h, const double* Y) { return h->frozen ? h->frozen : Y; }
+
 int rk_stages(sem_t h, const Tableau& T, double dt, const double* un, double* const* Y, double* unext,
               cudaStream_t s, long long& count) {
     const int last = unext ? T.s - 1 : T.s - 2;
+    if (subdiagonal(T)) {
+        // Y_{i+1} = un + dt a_{i+1,i} k_i and the running sum acc = un + dt sum_{j<=i} b_j k_j
+        // (vec(V_K0)); the last stage writes unext = acc + dt b_{s-1} k_{s-1}.
+        double* acc = vec(h, V_K0);
+        for (int i = 0; i <= last; ++i) {
+            Epi ep;
+            std::memset(&ep, 0, sizeof(ep));
+            ep.nonfinite = h->flag;
+            ep.f2 = f32(h);
+            if (i < T.s - 1) {
+                const int su = add_src(ep, un);
+                ep.out[0] = Y[i + 1];
+                ep.alpha[0] = dt * T.A[i + 1][i];
+                ep.beta[0][su] = 1.0;
+                ep.nout = 1;
+                if (unext) {
+                    const int sa = i == 0 ? su : add_src(ep, acc);
+                    ep.out[1] = acc;
+                    ep.alpha[1] = dt * T.b[i];
+                    ep.beta[1][sa] = 1.0;
+                    ep.nout = 2;
+                }
+            } else {
+                const int sa = T.s == 1 ? add_src(ep, un) : add_src(ep, acc);
+                ep.out[0] = unext;
+                ep.alpha[0] = dt * T.b[i];
+                ep.beta[0][sa] = 1.0;
+                ep.nout = 1;
+            }
+            SEM_TRY(stage_rhs(h, i == 0 ? un : Y[i], ep, s));
+            ++count;
+        }
+        return SEM_OK;
+    }
     for (int i = 0; i <= last; ++i) {
         const double* Yi = i == 0 ? un : Y[i];
         Epi ep;
@@ -354,7 +459,7 @@ int rk_stages(sem_t h, const Tableau& T, double dt, const double* un, double* co
                 if (T.b[j] != 0.0) ep.beta[0][add_src(ep, vec(h, V_K0 + j))] = dt * T.b[j];
             ep.nout = 1;
         }
-        SEM_TRY(apply(h, OP_RHS, Yi, nullptr, ep, s, f32(h)));
+        SEM_TRY(stage_rhs(h, Yi, ep, s));
         ++count;
     }
     return SEM_OK;
@@ -369,6 +474,42 @@ int rk_stages(sem_t h, const Tableau& T, double dt, const double* un, double* co
 int rk_adjoint_step(sem_t h, const Tableau& T, double dt, const double* const* Y, double* lam,
                     cudaStream_t s, long long& count) {
     double* nu = vec(h, V_NU);
+    if (subdiagonal(T) && T.s > 1) {
+        // nu_{i-1} = dt (b_{i-1} lam + a_{i,i-1} mu_i) and the running sum
+        // lacc = lam + sum_{j>=i} mu_j (vec(V_K0)); stage 0 writes lam = lacc + mu_0 and
+        // the next step's nu_{s-1} = dt b_{s-1} lam.
+        double* lacc = vec(h, V_K0);
+        for (int i = T.s - 1; i >= 0; --i) {
+            Epi ep;
+            std::memset(&ep, 0, sizeof(ep));
+            ep.nonfinite = h->flag;
+            ep.f2 = f32(h);
+            const int sl = add_src(ep, lam);
+            if (i > 0) {
+                ep.out[0] = nu;
+                ep.alpha[0] = dt * T.A[i][i - 1];
+                ep.beta[0][sl] = dt * T.b[i - 1];
+                const int sa = i == T.s - 1 ? sl : add_src(ep, lacc);
+                ep.out[1] = lacc;
+                ep.alpha[1] = 1.0;
+                ep.beta[1][sa] = 1.0;
+                ep.nout = 2;
+            } else {
+                const int sa = add_src(ep, lacc);
+                ep.out[0] = lam;
+                ep.alpha[0] = 1.0;
+                ep.beta[0][sa] = 1.0;
+                const double c = dt * T.b[T.s - 1];
+                ep.out[1] = nu;
+                ep.alpha[1] = c;
+                ep.beta[1][sa] = c;
+                ep.nout = 2;
+            }
+            SEM_TRY(apply(h, OP_JACT, jac_point(h, Y[i]), nu, ep, s, f32(h)));
+            ++count;
+        }
+        return SEM_OK;
+    }
     for (int i = T.s - 1; i >= 0; --i) {
         Epi ep;
         std::memset(&ep, 0, sizeof(ep));
@@ -395,7 +536,7 @@ int rk_adjoint_step(sem_t h, const Tableau& T, double dt, const double* const* Y
             for (int m = 0; m < ep.nsrc; ++m) ep.beta[1][m] = c * ep.beta[0][m];
             ep.nout = 2;
         }
-        SEM_TRY(apply(h, OP_JACT, Y[i], nu, ep, s, f32(h)));
+        SEM_TRY(apply(h, OP_JACT, jac_point(h, Y[i]), nu, ep, s, f32(h)));
         ++count;
     }
     return SEM_OK;
@@ -465,23 +606,28 @@ int check_flag(sem_t h, cudaStream_t s, const char* what) {
     return SEM_OK;
 }
 
+int cn_forward(sem_t h, double dt, int nsteps, const double* u0, double* uT, cudaStream_t s);
+int cn_adjoint(sem_t h, const double* lamT, double* lam0, cudaStream_t s);
+
 // uT_internal: uT is a handle work state (float pairs in the FP32 form) rather
 // than the caller's double output.
 int forward_impl(sem_t h, int scheme, double dt, int nsteps, const double* u0, double* uT, cudaStream_t s,
                  bool uT_internal = false) {
     Tableau T;
-    if (!tableau_of(scheme, T)) return fail(SEM_ERR_ARG, "unknown RK scheme %d", scheme);
+    if (scheme != SEM_CN && !tableau_of(scheme, T)) return fail(SEM_ERR_ARG, "unknown time scheme %d", scheme);
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(SEM_ERR_ARG, "dt must be finite and > 0");
     if (nsteps < 1) return fail(SEM_ERR_ARG, "nsteps must be >= 1");
     SEM_TRY(check_state_ptr(u0, "u0"));
     SEM_TRY(check_state_ptr(uT, "uT"));
     if (overlap(u0, uT, vec_bytes(h))) return fail(SEM_ERR_ALIAS, "uT overlaps u0");
     SEM_TRY(ensure_workspace(h));
+    if (scheme == SEM_CN) return cn_forward(h, dt, nsteps, u0, uT, s);
     int mode, slots;
     SEM_TRY(choose_mode(h, T.s, nsteps, mode, slots));
     if (mode == SEM_CKPT_BINOMIAL && slots > nsteps) slots = nsteps;
+    if (h->frozen) mode = MODE_LINEAR;   // the adjoint needs no stage values
     const size_t nvec = mode == SEM_CKPT_STAGES ? (size_t)nsteps * T.s : (mode == SEM_CKPT_STATES ? (size_t)nsteps : (size_t)slots);
-    SEM_TRY(alloc_traj(h, nvec));
+    if (mode != MODE_LINEAR) SEM_TRY(alloc_traj(h, nvec));
     h->have_fwd = false;
     const size_t vb = vec_bytes(h);
     double* Yw[4] = {nullptr, vec(h, V_STAGE0), vec(h, V_STAGE0 + 1), vec(h, V_STAGE0 + 2)};
@@ -500,7 +646,15 @@ int forward_impl(sem_t h, int scheme, double dt, int nsteps, const double* u0, d
         }
         return SEM_OK;
     };
-    if (mode == SEM_CKPT_STAGES) {
+    if (mode == MODE_LINEAR) {
+        SEM_TRY(put_u0(vec(h, V_CUR0)));
+        const double* cur = vec(h, V_CUR0);
+        for (int n = 0; n < nsteps; ++n) {
+            double* next = n + 1 == nsteps ? uT : (cur == vec(h, V_CUR0) ? vec(h, V_CUR1) : vec(h, V_CUR0));
+            SEM_TRY(rk_stages(h, T, dt, cur, Yw, next, s, count));
+            cur = next;
+        }
+    } else if (mode == SEM_CKPT_STAGES) {
         SEM_TRY(put_u0(h->traj));
         for (int n = 0; n < nsteps; ++n) {
             double* base = h->traj + (size_t)n * T.s * h->ndof;
@@ -551,6 +705,7 @@ int adjoint_impl(sem_t h, const double* lamT, double* lam0, cudaStream_t s, bool
     if (!lam_internal) SEM_TRY(check_state_ptr(lamT, "lamT"));
     SEM_TRY(check_state_ptr(lam0, "lam0"));
     if (lamT != lam0 && overlap(lamT, lam0, vec_bytes(h))) return fail(SEM_ERR_ALIAS, "lam0 partially overlaps lamT");
+    if (h->f_scheme == SEM_CN) return cn_adjoint(h, lamT, lam0, s);
     Tableau T;
     tableau_of(h->f_scheme, T);
     const double dt = h->f_dt;
@@ -573,7 +728,11 @@ int adjoint_impl(sem_t h, const double* lamT, double* lam0, cudaStream_t s, bool
     }
     long long nrhs = 0, njt = 0;
     double* Yw[4] = {nullptr, vec(h, V_STAGE0), vec(h, V_STAGE0 + 1), vec(h, V_STAGE0 + 2)};
-    if (h->f_mode == SEM_CKPT_STAGES) {
+    if (h->f_mode == MODE_LINEAR) {
+        if (!h->frozen) return fail(SEM_ERR_STATE, "the advecting field changed after the forward sweep");
+        const double* Y[4] = {h->frozen, h->frozen, h->frozen, h->frozen};
+        for (int n = nsteps - 1; n >= 0; --n) SEM_TRY(rk_adjoint_step(h, T, dt, Y, lam0, s, njt));
+    } else if (h->f_mode == SEM_CKPT_STAGES) {
         for (int n = nsteps - 1; n >= 0; --n) {
             double* base = h->traj + (size_t)n * T.s * h->ndof;
             const double* Y[4] = {base, base + h->ndof, base + 2 * h->ndof, base + 3 * h->ndof};
@@ -638,6 +797,278 @@ int objective_impl(sem_t h, const double* u, const double* uo, double* lam, cuda
                              : launch_objective(u, uo, lam, h->partials, nb, a, s);
     if (e == cudaSuccess) e = launch_sum_partials(h->partials, nb, h->scal, 0.5, s);
     if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "objective launch: %s", cudaGetErrorString(e));
+    return SEM_OK;
+}
+
+// ------------------------------------------------------------------ Crank-Nicolson
+// The implicit scheme of Sec. 6.3.  Step: R(v) = v - u_n - dt/2 (F(u_n) + F(v)) = 0
+// by Newton, (I - dt/2 J(v)) delta = -R(v), each linear system by restarted GMRES;
+// discrete adjoint: (I - dt/2 J(u_{n+1})^T) mu = lam_{n+1}, lam_n = mu + dt/2 J(u_n)^T mu.
+// The Newton right-hand side and the products (I - c J) x are operator applies
+// whose assembly epilogue adds the shifts, so every step runs in the library's
+// kernels.  GMRES keeps its basis on the device (classical Gram-Schmidt with one
+// re-orthogonalisation, coefficients never leave the device) and reads back the
+// new Hessenberg column once per Arnoldi step for the Givens rotations.
+constexpr int KSCAL_ONE = 2 * KMAX;   // kscal[KSCAL_ONE] == 1.0
+
+int krylov_ws(sem_t h) {
+    if (h->kbasis) return SEM_OK;
+    cudaError_t e = cudaMalloc((void**)&h->kbasis, vec_bytes(h) * (h->krylov_m + 2));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->kpart, sizeof(double) * KMAX * multidot_blocks(h->ndof));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->kscal, sizeof(double) * (KSCAL_ONE + 1));
+    if (e == cudaSuccess) {
+        const double one = 1.0;
+        e = cudaMemcpy(h->kscal + KSCAL_ONE, &one, sizeof(double), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(h->kbasis);
+        cudaFree(h->kpart);
+        cudaFree(h->kscal);
+        h->kbasis = nullptr;
+        h->kpart = h->kscal = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? SEM_ERR_OOM : SEM_ERR_CUDA, "Krylov workspace: %s",
+                    cudaGetErrorString(e));
+    }
+    return SEM_OK;
+}
+
+double* kvec(sem_t h, int j) { return h->kbasis + (size_t)j * h->ndof; }
+
+// device scalars out[0..k) = <V_j, w>
+int dots(sem_t h, const double* const* V, int k, const double* w, double* out, cudaStream_t s) {
+    VecList L;
+    for (int j = 0; j < k; ++j) L.v[j] = V[j];
+    cudaError_t e = launch_multidot(L, k, w, h->ndof, h->kpart, out, s);
+    if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "multidot launch: %s", cudaGetErrorString(e));
+    return SEM_OK;
+}
+
+// w += sign * sum_j coef[j] V_j (coef on the device)
+int axpys(sem_t h, double* w, const double* const* V, int k, const double* coef, double sign, cudaStream_t s) {
+    VecList L;
+    for (int j = 0; j < k; ++j) L.v[j] = V[j];
+    cudaError_t e = launch_multiaxpy(w, L, k, coef, sign, h->ndof, s);
+    if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "multiaxpy launch: %s", cudaGetErrorString(e));
+    return SEM_OK;
+}
+
+int host_norm(sem_t h, const double* a, cudaStream_t s, double& out) {
+    SEM_TRY(dots(h, &a, 1, a, h->kscal + KMAX, s));
+    double v = 0.0;
+    SEM_CK(cudaMemcpyAsync(&v, h->kscal + KMAX, sizeof(double), cudaMemcpyDeviceToHost, s));
+    SEM_CK(cudaStreamSynchronize(s));
+    out = std::sqrt(v);
+    return SEM_OK;
+}
+
+// out = sb * b + sx * x + so * Op(u) x  with Op = J (OP_JAC) or J^T (OP_JACT); b may be null
+int shifted(sem_t h, int op, const double* u, double so, const double* x, double sx, const double* b, double sb,
+            double* out, cudaStream_t s) {
+    Epi ep;
+    std::memset(&ep, 0, sizeof(ep));
+    ep.nonfinite = h->flag;
+    ep.out[0] = out;
+    ep.alpha[0] = so;
+    ep.src[0] = x;
+    ep.beta[0][0] = sx;
+    ep.nsrc = 1;
+    if (b) {
+        ep.src[1] = b;
+        ep.beta[0][1] = sb;
+        ep.nsrc = 2;
+    }
+    ep.nout = 1;
+    ++h->cn_st[3];
+    return apply(h, op, u, x, ep, s);
+}
+
+// Solve (I - c Op(u)) x = b by restarted GMRES(m) from x = 0 to |b - A x| <= rtol |b|;
+// its accumulates the Arnoldi steps.
+int gmres(sem_t h, int op, const double* u, double c, const double* b, double* x, cudaStream_t s, long long& its) {
+    SEM_TRY(krylov_ws(h));
+    const int m = h->krylov_m;
+    double* w = kvec(h, m + 1);
+    SEM_CK(cudaMemsetAsync(x, 0, vec_bytes(h), s));
+    double bnorm = 0.0;
+    SEM_TRY(host_norm(h, b, s, bnorm));
+    if (bnorm == 0.0) return SEM_OK;
+    if (!std::isfinite(bnorm)) return fail(SEM_ERR_NONFINITE, "non-finite right-hand side of a linear solve");
+    const double tol = h->krylov_rtol * bnorm;
+    double beta = bnorm;
+    const double* r = b;
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), h1(m + 2), h2(m + 2), y(m);
+    long long total = 0;
+    for (;;) {
+        cudaError_t e = launch_scale(kvec(h, 0), r, 1.0 / beta, h->ndof, s);   // v_0 = r / beta
+        if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "scale launch: %s", cudaGetErrorString(e));
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int j = 0;
+        bool done = false;
+        while (j < m && total < h->krylov_maxit) {
+            SEM_TRY(shifted(h, op, u, -c, kvec(h, j), 1.0, nullptr, 0.0, w, s));   // w = A v_j
+            const double* V[KMAX];
+            for (int i = 0; i <= j; ++i) V[i] = kvec(h, i);
+            SEM_TRY(dots(h, V, j + 1, w, h->kscal, s));
+            SEM_TRY(axpys(h, w, V, j + 1, h->kscal, -1.0, s));
+            SEM_TRY(dots(h, V, j + 1, w, h->kscal + KMAX, s));
+            SEM_TRY(axpys(h, w, V, j + 1, h->kscal + KMAX, -1.0, s));
+            const double* ww = w;
+            SEM_TRY(dots(h, &ww, 1, w, h->kscal + KMAX + j + 1, s));
+            SEM_CK(cudaMemcpyAsync(h1.data(), h->kscal, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, s));
+            SEM_CK(cudaMemcpyAsync(h2.data(), h->kscal + KMAX, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
+            SEM_CK(cudaStreamSynchronize(s));
+            ++total;
+            double* col = &H[0];
+            for (int i = 0; i <= j; ++i) col[(size_t)i * m + j] = h1[i] + h2[i];
+            const double hn = std::sqrt(std::max(h2[j + 1], 0.0));
+            for (int i = 0; i < j; ++i) {   // apply the earlier rotations to column j
+                const double a0 = col[(size_t)i * m + j], a1 = col[(size_t)(i + 1) * m + j];
+                col[(size_t)i * m + j] = cs[i] * a0 + sn[i] * a1;
+                col[(size_t)(i + 1) * m + j] = -sn[i] * a0 + cs[i] * a1;
+            }
+            const double a0 = col[(size_t)j * m + j];
+            const double rr = std::hypot(a0, hn);
+            if (!(rr > 0.0) || !std::isfinite(rr)) return fail(SEM_ERR_NONFINITE, "GMRES breakdown (column norm %g)", rr);
+            cs[j] = a0 / rr;
+            sn[j] = hn / rr;
+            col[(size_t)j * m + j] = rr;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            ++j;
+            if (std::fabs(g[j]) <= tol || hn == 0.0) {
+                done = true;
+                break;
+            }
+            if (j < m) {
+                e = launch_scale(kvec(h, j), w, 1.0 / hn, h->ndof, s);
+                if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "scale launch: %s", cudaGetErrorString(e));
+            }
+        }
+        // x += V y with R y = g (the rotated Hessenberg matrix is upper triangular)
+        for (int i = j - 1; i >= 0; --i) {
+            double acc = g[i];
+            for (int l = i + 1; l < j; ++l) acc -= H[(size_t)i * m + l] * y[l];
+            y[i] = acc / H[(size_t)i * m + i];
+        }
+        SEM_CK(cudaMemcpyAsync(h->kscal, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
+        const double* V[KMAX];
+        for (int i = 0; i < j; ++i) V[i] = kvec(h, i);
+        SEM_TRY(axpys(h, x, V, j, h->kscal, 1.0, s));
+        if (done) break;
+        if (total >= h->krylov_maxit)
+            return fail(SEM_ERR_NONFINITE, "GMRES did not reach relative residual %.1e in %d steps", h->krylov_rtol,
+                        h->krylov_maxit);
+        SEM_TRY(shifted(h, op, u, c, x, -1.0, b, 1.0, w, s));   // restart from r = b - x + c Op x = b - A x
+        SEM_TRY(host_norm(h, w, s, beta));
+        if (!std::isfinite(beta)) return fail(SEM_ERR_NONFINITE, "non-finite GMRES residual");
+        if (beta <= tol) break;
+        r = w;
+    }
+    its += total;
+    return SEM_OK;
+}
+
+// One CN step u -> u_next by Newton's method (explicit Euler predictor).
+int cn_step(sem_t h, double dt, const double* u, double* u_next, cudaStream_t s) {
+    double* Fn = vec(h, V_K0);
+    double* b = vec(h, V_K0 + 1);
+    double* delta = vec(h, V_K0 + 2);
+    {   // Fn = F(u), u_next = u + dt Fn
+        Epi ep;
+        std::memset(&ep, 0, sizeof(ep));
+        ep.nonfinite = h->flag;
+        ep.out[0] = Fn;
+        ep.alpha[0] = 1.0;
+        ep.out[1] = u_next;
+        ep.alpha[1] = dt;
+        ep.src[0] = u;
+        ep.beta[1][0] = 1.0;
+        ep.nsrc = 1;
+        ep.nout = 2;
+        ++h->cn_st[3];
+        ++h->st[0];
+        SEM_TRY(stage_rhs(h, u, ep, s));
+    }
+    for (int it = 0; it < h->newton_maxit; ++it) {
+        {   // b = -R(v) = dt/2 F(v) - v + u + dt/2 Fn
+            Epi ep;
+            std::memset(&ep, 0, sizeof(ep));
+            ep.nonfinite = h->flag;
+            ep.out[0] = b;
+            ep.alpha[0] = 0.5 * dt;
+            ep.src[0] = u_next;
+            ep.beta[0][0] = -1.0;
+            ep.src[1] = u;
+            ep.beta[0][1] = 1.0;
+            ep.src[2] = Fn;
+            ep.beta[0][2] = 0.5 * dt;
+            ep.nsrc = 3;
+            ep.nout = 1;
+            ++h->cn_st[3];
+            ++h->st[0];
+            SEM_TRY(stage_rhs(h, u_next, ep, s));
+        }
+        SEM_TRY(gmres(h, OP_JAC, jac_point(h, u_next), 0.5 * dt, b, delta, s, h->cn_st[1]));
+        ++h->cn_st[0];
+        const double* Vd = delta;
+        SEM_TRY(axpys(h, u_next, &Vd, 1, h->kscal + KSCAL_ONE, 1.0, s));
+        double dn = 0.0, vn = 0.0;
+        SEM_TRY(host_norm(h, delta, s, dn));
+        SEM_TRY(host_norm(h, u_next, s, vn));
+        if (!std::isfinite(dn) || !std::isfinite(vn)) return fail(SEM_ERR_NONFINITE, "non-finite Newton iterate");
+        if (dn <= h->newton_rtol * std::max(vn, 1.0)) return SEM_OK;
+    }
+    return fail(SEM_ERR_NONFINITE, "Newton did not converge in %d iterations", h->newton_maxit);
+}
+
+// Forward sweep storing every state u_0 .. u_N (the adjoint needs both ends of each step).
+int cn_forward(sem_t h, double dt, int nsteps, const double* u0, double* uT, cudaStream_t s) {
+    if (f32(h)) return fail(SEM_ERR_ARG, "the Crank-Nicolson scheme runs in the FP64 form only");
+    if (h->batch) return fail(SEM_ERR_ARG, "the Crank-Nicolson scheme is not available for batches");
+    SEM_TRY(alloc_traj(h, (size_t)nsteps + 1));
+    h->have_fwd = false;
+    for (int k = 0; k < 4; ++k) h->cn_st[k] = 0;
+    h->st[0] = h->st[1] = h->st[2] = 0;
+    SEM_CK(cudaMemcpyAsync(h->traj, u0, vec_bytes(h), cudaMemcpyDeviceToDevice, s));
+    for (int n = 0; n < nsteps; ++n)
+        SEM_TRY(cn_step(h, dt, h->traj + (size_t)n * h->ndof, h->traj + (size_t)(n + 1) * h->ndof, s));
+    SEM_CK(cudaMemcpyAsync(uT, h->traj + (size_t)nsteps * h->ndof, vec_bytes(h), cudaMemcpyDeviceToDevice, s));
+    h->have_fwd = true;
+    h->f_scheme = SEM_CN;
+    h->f_nsteps = nsteps;
+    h->f_dt = dt;
+    h->f_mode = SEM_CKPT_STATES;
+    h->f_slots = 0;
+    h->f_ckpt.clear();
+    return SEM_OK;
+}
+
+int cn_adjoint(sem_t h, const double* lamT, double* lam0, cudaStream_t s) {
+    const double dt = h->f_dt;
+    double* mu = vec(h, V_NU);
+    h->cn_st[2] = 0;
+    h->st[2] = 0;
+    if (lam0 != lamT) SEM_CK(cudaMemcpyAsync(lam0, lamT, vec_bytes(h), cudaMemcpyDeviceToDevice, s));
+    for (int n = h->f_nsteps - 1; n >= 0; --n) {
+        const double* un1 = h->traj + (size_t)(n + 1) * h->ndof;
+        const double* un = h->traj + (size_t)n * h->ndof;
+        const long long before = h->cn_st[3];
+        SEM_TRY(gmres(h, OP_JACT, jac_point(h, un1), 0.5 * dt, lam0, mu, s, h->cn_st[2]));
+        Epi ep;   // lam_n = mu + dt/2 J(u_n)^T mu
+        std::memset(&ep, 0, sizeof(ep));
+        ep.nonfinite = h->flag;
+        ep.out[0] = lam0;
+        ep.alpha[0] = 0.5 * dt;
+        ep.src[0] = mu;
+        ep.beta[0][0] = 1.0;
+        ep.nsrc = 1;
+        ep.nout = 1;
+        ++h->cn_st[3];
+        SEM_TRY(apply(h, OP_JACT, jac_point(h, un), mu, ep, s));
+        h->st[2] += h->cn_st[3] - before;
+    }
     return SEM_OK;
 }
 
@@ -827,12 +1258,17 @@ void sem_destroy(sem_t h) {
     }
     if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
     if (h->graph_stream) cudaStreamDestroy(h->graph_stream);
+    prof_graph_release(h);
     cudaFree(h->lvec);
     cudaFree(h->partials);
     cudaFree(h->scal);
     cudaFree(h->flag);
     cudaFree(h->vecs);
     cudaFree(h->traj);
+    cudaFree(h->kbasis);
+    cudaFree(h->kpart);
+    cudaFree(h->kscal);
+    cudaFree(h->frozen);
     if (h->batch) {
         BatchHost* b = h->batch;
         cudaFree(b->d_inst);
@@ -959,20 +1395,26 @@ static int objective_grad_graph(sem_t h, int scheme, double dt, int nsteps, cons
         int mode, slots;
         SEM_TRY(choose_mode(h, T.s, nsteps, mode, slots));
         if (mode == SEM_CKPT_BINOMIAL && slots > nsteps) slots = nsteps;
-        SEM_TRY(alloc_traj(h, mode == SEM_CKPT_STAGES ? (size_t)nsteps * T.s
-                                 : (mode == SEM_CKPT_STATES ? (size_t)nsteps : (size_t)slots)));
+        if (!h->frozen)
+            SEM_TRY(alloc_traj(h, mode == SEM_CKPT_STAGES ? (size_t)nsteps * T.s
+                                     : (mode == SEM_CKPT_STATES ? (size_t)nsteps : (size_t)slots)));
         if (h->batch && !h->batch->threads) SEM_TRY(batch_tune(h, s));
         if (!h->graph_stream) SEM_CK(cudaStreamCreateWithFlags(&h->graph_stream, cudaStreamNonBlocking));
         SEM_CK(cudaStreamSynchronize(s));
-        const int prof = h->prof;
-        h->prof = 0;
         h->fixed_mode = mode;
         h->fixed_slots = slots;
+        if (h->graph_exec) {
+            cudaGraphExecDestroy(h->graph_exec);
+            h->graph_exec = nullptr;
+        }
+        prof_graph_release(h);
+        for (int i = 0; i < 4; ++i) h->prof_tick[i] = 0;
         cudaGraph_t g = nullptr;
         SEM_CK(cudaStreamBeginCapture(h->graph_stream, cudaStreamCaptureModeThreadLocal));
+        h->capturing = true;
         const int rc = objective_grad_launches(h, scheme, dt, nsteps, u0, uo, grad, h->graph_stream);
+        h->capturing = false;
         cudaError_t ec = cudaStreamEndCapture(h->graph_stream, &g);
-        h->prof = prof;
         h->fixed_mode = -1;
         if (rc != SEM_OK) {
             if (g) cudaGraphDestroy(g);
@@ -1002,12 +1444,15 @@ int sem_objective_grad(sem_t h, int scheme, double dt, int nsteps, const double*
     if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 1) return fail(SEM_ERR_ARG, "dt > 0 and nsteps >= 1");
     SEM_TRY(ensure_workspace(h));
     cudaStream_t s = (cudaStream_t)stream;
-    if (h->graph_on) SEM_TRY(objective_grad_graph(h, scheme, dt, nsteps, u0, uo, grad, s));
+    // the implicit scheme synchronises with the host inside its solves: never captured
+    const bool graph = h->graph_on && scheme != SEM_CN;
+    if (graph) SEM_TRY(objective_grad_graph(h, scheme, dt, nsteps, u0, uo, grad, s));
     else SEM_TRY(objective_grad_launches(h, scheme, dt, nsteps, u0, uo, grad, s));
     unsigned f = 0;
     SEM_CK(cudaMemcpyAsync(J_host, h->scal, sizeof(double), cudaMemcpyDeviceToHost, s));
     SEM_CK(cudaMemcpyAsync(&f, h->flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     SEM_CK(cudaStreamSynchronize(s));
+    if (graph && h->prof) SEM_TRY(prof_graph_accumulate(h));
     if (f || !std::isfinite(*J_host)) return fail(SEM_ERR_NONFINITE, "non-finite values in the gradient evaluation");
     return SEM_OK;
 }
@@ -1019,6 +1464,7 @@ int sem_set_graph(sem_t h, int enable) {
         cudaGraphExecDestroy(h->graph_exec);
         h->graph_exec = nullptr;
         h->graph_key = sem_ctx::GraphKey{-1, 0, 0.0, nullptr, nullptr, nullptr};
+        prof_graph_release(h);
     }
     return SEM_OK;
 }
@@ -1035,6 +1481,71 @@ int sem_ckpt_plan(int nsteps, int slots, long long* advances) {
 int sem_sweep_stats(sem_t h, long long* out3) {
     if (!h || !out3) return fail(SEM_ERR_ARG, "null handle or output");
     for (int i = 0; i < 3; ++i) out3[i] = h->st[i];
+    return SEM_OK;
+}
+
+int sem_set_advection(sem_t h, const double* a, void* stream) {
+    if (!h) return fail(SEM_ERR_ARG, "null handle");
+    cudaStream_t s = (cudaStream_t)stream;
+    // a recorded gradient graph and a recorded forward sweep belong to the previous equation
+    if (h->graph_exec) {
+        SEM_CK(cudaStreamSynchronize(s));
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+        h->graph_key = sem_ctx::GraphKey{-1, 0, 0.0, nullptr, nullptr, nullptr};
+        prof_graph_release(h);
+    }
+    h->have_fwd = false;
+    if (!a) {
+        if (h->frozen) {
+            SEM_CK(cudaStreamSynchronize(s));
+            cudaFree(h->frozen);
+            h->frozen = nullptr;
+        }
+        return SEM_OK;
+    }
+    SEM_TRY(check_state_ptr(a, "a"));
+    SEM_TRY(ensure_workspace(h));
+    if (!h->frozen) {
+        cudaError_t e = cudaMalloc((void**)&h->frozen, vec_bytes(h));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->frozen = nullptr;
+            return fail(e == cudaErrorMemoryAllocation ? SEM_ERR_OOM : SEM_ERR_CUDA, "advecting field: %s",
+                        cudaGetErrorString(e));
+        }
+    }
+    if (f32(h)) {
+        cudaError_t e = launch_f64_to_f2(a, fl(h->frozen), h->ndof, s);
+        if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "conversion launch: %s", cudaGetErrorString(e));
+    } else {
+        SEM_CK(cudaMemcpyAsync(h->frozen, a, vec_bytes(h), cudaMemcpyDeviceToDevice, s));
+    }
+    return SEM_OK;
+}
+
+int sem_set_solver(sem_t h, double newton_rtol, double krylov_rtol, int krylov_m, int krylov_maxit) {
+    if (!h) return fail(SEM_ERR_ARG, "null handle");
+    if (!(newton_rtol > 0.0) || !(krylov_rtol > 0.0) || krylov_m < 1 || krylov_m > KMAX - 2 || krylov_maxit < 1)
+        return fail(SEM_ERR_ARG, "tolerances must be > 0, 1 <= krylov_m <= %d, krylov_maxit >= 1", KMAX - 2);
+    if (krylov_m != h->krylov_m) {
+        if (h->kbasis) SEM_CK(cudaDeviceSynchronize());
+        cudaFree(h->kbasis);
+        cudaFree(h->kpart);
+        cudaFree(h->kscal);
+        h->kbasis = nullptr;
+        h->kpart = h->kscal = nullptr;
+    }
+    h->newton_rtol = newton_rtol;
+    h->krylov_rtol = krylov_rtol;
+    h->krylov_m = krylov_m;
+    h->krylov_maxit = krylov_maxit;
+    return SEM_OK;
+}
+
+int sem_solver_stats(sem_t h, long long* out4) {
+    if (!h || !out4) return fail(SEM_ERR_ARG, "null handle or output");
+    for (int i = 0; i < 4; ++i) out4[i] = h->cn_st[i];
     return SEM_OK;
 }
 

@@ -120,6 +120,17 @@ cudaError_t launch_objective_f2(const float* u, const double* uo, float* lam, do
 // out <- alpha * in for float-pair vectors (pair arithmetic)
 cudaError_t launch_scale_f2(float* out, const float* in, double alpha, size_t n, cudaStream_t s);
 
+// Krylov helpers (FP64): out[j] = <V_j, w> for j < k in one pass, fixed summation
+// order (per-block partials, then one block per j); w <- w + sum_j coef[j] V_j with
+// coef on the device (scale = +1 or -1, the sign of the update).  k <= KMAX.
+constexpr int KMAX = 40;
+struct VecList { const double* v[KMAX]; };
+int multidot_blocks(size_t n);
+cudaError_t launch_multidot(const VecList& V, int k, const double* w, size_t n, double* partials, double* out,
+                            cudaStream_t s);
+cudaError_t launch_multiaxpy(double* w, const VecList& V, int k, const double* coef, double scale, size_t n,
+                             cudaStream_t s);
+
 // out <- alpha * in  (n doubles)
 cudaError_t launch_scale(double* out, const double* in, double alpha, size_t n, cudaStream_t s);
 

@@ -493,4 +493,80 @@ cudaError_t launch_objective_f2(const float* u, const double* uo, float* lam, do
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ Krylov helpers
+constexpr int MD_THREADS = 256;
+
+int multidot_blocks(size_t n) {
+    size_t b = (n + MD_THREADS * 4 - 1) / (MD_THREADS * 4);
+    if (b > 608) b = 608;
+    return (int)(b ? b : 1);
+}
+
+// partials[j * gridDim.x + block] = sum over the block's strided range of V_j[i] w[i]
+__global__ void __launch_bounds__(MD_THREADS) multidot_kernel(const VecList V, int k,
+                                                              const double* __restrict__ w, size_t n,
+                                                              double* __restrict__ partials) {
+    __shared__ double ws[MD_THREADS / 32];
+    for (int j = 0; j < k; ++j) {
+        double acc = 0.0;
+        const double* __restrict__ vj = V.v[j];
+        for (size_t i = blockIdx.x * (size_t)MD_THREADS + threadIdx.x; i < n; i += (size_t)gridDim.x * MD_THREADS)
+            acc = fma(vj[i], w[i], acc);
+        acc = warp_sum(acc);
+        if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double v = threadIdx.x < MD_THREADS / 32 ? ws[threadIdx.x] : 0.0;
+            v = warp_sum(v);
+            if (threadIdx.x == 0) partials[(size_t)j * gridDim.x + blockIdx.x] = v;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) multidot_final(const double* __restrict__ partials, int nb,
+                                                      double* __restrict__ out) {
+    __shared__ double ws[8];
+    const int j = blockIdx.x;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += partials[(size_t)j * nb + b];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < 8 ? ws[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) out[j] = v;
+    }
+}
+
+cudaError_t launch_multidot(const VecList& V, int k, const double* w, size_t n, double* partials, double* out,
+                            cudaStream_t s) {
+    if (k <= 0) return cudaSuccess;
+    const int nb = multidot_blocks(n);
+    multidot_kernel<<<nb, MD_THREADS, 0, s>>>(V, k, w, n, partials);
+    multidot_final<<<k, 256, 0, s>>>(partials, nb, out);
+    return cudaGetLastError();
+}
+
+// w += sum_j (+-coef[j]) V_j; the sign is an operand modifier of the FMA (no extra FP64 multiply)
+template <bool NEG>
+__global__ void multiaxpy_kernel(double* __restrict__ w, const VecList V, int k, const double* __restrict__ coef,
+                                 size_t n) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        double acc = w[i];
+        for (int j = 0; j < k; ++j) acc = fma(NEG ? -coef[j] : coef[j], V.v[j][i], acc);
+        w[i] = acc;
+    }
+}
+
+cudaError_t launch_multiaxpy(double* w, const VecList& V, int k, const double* coef, double scale, size_t n,
+                             cudaStream_t s) {
+    if (k <= 0 || n == 0) return cudaSuccess;
+    if (scale < 0) multiaxpy_kernel<true><<<grid_for(n), 256, 0, s>>>(w, V, k, coef, n);
+    else multiaxpy_kernel<false><<<grid_for(n), 256, 0, s>>>(w, V, k, coef, n);
+    return cudaGetLastError();
+}
+
 }  // namespace semk

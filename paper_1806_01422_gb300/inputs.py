@@ -18,6 +18,15 @@ the x_0 direction, component c the velocity along x_c):
   scaled so max |u| = 1, on [0, 1)^3; evaluated separably through complex
   exponentials per axis.
 * ``field_random``: i.i.d. N(0,1) nodal values (operator parity inputs).
+
+Exact solutions of the PDE used as data for the inverse problems of Sec. 6.1:
+
+* ``advection_diffusion_1d``: u = sum_{j=1..5} c_j sin(2 pi j (x - a t)) exp(-4 pi^2 j^2 nu t),
+  the solution of u_t + a u_x = nu u_xx on the unit period (coefficients c_j ~ U(0.9, 1)
+  from ``advection_diffusion_coefs``).
+* ``cole_hopf_1d``: the Cole-Hopf solution of viscous Burgers
+  u = 2 nu pi sin(pi x) e / (2 + e cos(pi x)), e = exp(-nu pi^2 t), period 2; and
+  ``gaussian_bump`` = exp(-4 (x - 2)^2), the perturbation of its initial guess.
 """
 import numpy as np
 
@@ -97,3 +106,23 @@ def workload_field(dim, x, seed):
     if dim == 2:
         return field_2d(x, seed)
     return field_3d(x, seed)
+
+
+def advection_diffusion_coefs(seed, modes=5):
+    return np.random.default_rng(seed).uniform(0.9, 1.0, modes)
+
+
+def advection_diffusion_1d(x, t, coefs, nu, speed):
+    u = np.zeros_like(x, dtype=np.float64)
+    for j, c in enumerate(coefs, start=1):
+        u += c * np.sin(2.0 * np.pi * j * (x - speed * t)) * np.exp(-4.0 * np.pi ** 2 * j * j * nu * t)
+    return u[None, :]
+
+
+def cole_hopf_1d(x, t, nu):
+    e = np.exp(-nu * t * np.pi ** 2)
+    return (2.0 * nu * np.pi * np.sin(np.pi * x) * e / (2.0 + e * np.cos(np.pi * x)))[None, :]
+
+
+def gaussian_bump(x):
+    return np.exp(-4.0 * (x - 2.0) ** 2)[None, :]

@@ -6,6 +6,8 @@
     python -m paper_1806_01422_gb300.ncu_summary report FILE.ncu-rep
         per captured launch: duration, DRAM bytes, pipe utilisation, warps,
         registers and the main stall reasons (needs the `ncu` CLI to export)
+    python -m paper_1806_01422_gb300.ncu_summary raw FILE.csv
+        the same from `ncu -i FILE.ncu-rep --page raw --csv` output
 """
 import collections
 import csv
@@ -59,9 +61,10 @@ def launches(path):
     return "\n".join(out)
 
 
-def report(path):
-    raw = subprocess.run(["ncu", "-i", path, "--page", "raw", "--csv"], capture_output=True, text=True,
-                         check=True).stdout
+def report(path, raw=None):
+    if raw is None:
+        raw = subprocess.run(["ncu", "-i", path, "--page", "raw", "--csv"], capture_output=True, text=True,
+                             check=True).stdout
     rows = list(csv.reader(io.StringIO(raw)))
     h, units = rows[0], rows[1]
     out = []
@@ -80,4 +83,9 @@ def report(path):
 
 if __name__ == "__main__":
     kind, path = sys.argv[1], sys.argv[2]
-    print(launches(path) if kind == "launches" else report(path))
+    if kind == "launches":
+        print(launches(path))
+    elif kind == "raw":
+        print(report(None, raw=open(path).read()))
+    else:
+        print(report(path))

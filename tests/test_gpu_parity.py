@@ -281,3 +281,18 @@ def test_graph_replay_equals_stream_launches(mode, slots):
         J1, g1 = s.objective_grad(u0, uo, 2e-4, 9, "ssprk3", grad=grad)
         assert J1 == J0 and torch.equal(g1, g0)
     assert s.graph_replays() == 3
+
+
+def test_kernel_timing_inside_a_replayed_graph():
+    s, g = pair(2, 6, 7, nu=1e-3)
+    u0, uo = torch.from_numpy(smooth(g, 1)).cuda(), torch.from_numpy(smooth(g, 2)).cuda()
+    s.profile(4)
+    s.use_graph(True)
+    s.objective_grad(u0, uo, 2e-4, 8, "ssprk3")        # records the graph, then replays it
+    first = s.profile_read(reset=True)
+    s.objective_grad(u0, uo, 2e-4, 8, "ssprk3")        # replay only
+    second = s.profile_read(reset=True)
+    # 8 steps x 3 stages of F and of J^T, one in 4 of each kind timed, every replay
+    assert second["rhs"][1] == 6 and second["jacT"][1] == 6 and second["assemble"][1] == 12
+    assert first["rhs"][1] == second["rhs"][1]
+    assert all(second[k][0] > 0 for k in ("rhs", "jacT", "assemble"))

@@ -1,0 +1,36 @@
+"""L-BFGS with the Moré-Thuente line search on problems with known minimisers (CPU)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1806_01422_gb300.lbfgs import lbfgs, more_thuente
+
+
+def test_line_search_satisfies_strong_wolfe_on_a_quartic():
+    # phi(t) = (t - 2)^4 - t: minimiser where 4 (t - 2)^3 = 1
+    phi = lambda t: ((t - 2) ** 4 - t, 4 * (t - 2) ** 3 - 1, None)
+    f0, g0, _ = phi(0.0)
+    t, f, _, n = more_thuente(phi, f0, g0, stp=1.0, ftol=1e-4, gtol=0.1)
+    assert f <= f0 + 1e-4 * t * g0
+    assert abs(phi(t)[1]) <= 0.1 * abs(g0)
+
+
+def test_quadratic_is_minimised_to_the_exact_solution():
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((30, 30))
+    A = torch.from_numpy(A @ A.T + 30 * np.eye(30))
+    b = torch.from_numpy(rng.standard_normal(30))
+    fg = lambda x: (float(0.5 * x @ A @ x - b @ x), A @ x - b)
+    x, hist = lbfgs(fg, torch.zeros(30, dtype=torch.float64), m=10, max_iter=200, gtol=1e-12)
+    assert torch.allclose(x, torch.linalg.solve(A, b), rtol=1e-9, atol=1e-10)
+    assert all(h2[1] <= h1[1] for h1, h2 in zip(hist, hist[1:]))   # monotone decrease
+
+
+def test_rosenbrock_converges():
+    def fg(x):
+        a, b = x[0], x[1]
+        f = (1 - a) ** 2 + 100 * (b - a * a) ** 2
+        g = torch.stack([-2 * (1 - a) - 400 * a * (b - a * a), 200 * (b - a * a)])
+        return float(f), g
+    x, hist = lbfgs(fg, torch.tensor([-1.2, 1.0], dtype=torch.float64), m=6, max_iter=200, gtol=1e-10)
+    assert torch.allclose(x, torch.tensor([1.0, 1.0], dtype=torch.float64), atol=1e-6)

@@ -16,6 +16,7 @@ from oracle.gll import gll
 from oracle.sem import Grid
 from oracle import rk as ork
 from oracle.checkpoint import optimal_advances, checkpointed_gradient_lam0
+from paper_1806_01422_gb300 import inputs
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -380,3 +381,22 @@ def test_cn_tangent_adjoint_duality_and_gradient():
     fd = (ocn.cn_objective_and_gradient(g, u0 + eps * du0, uo, dt, steps)[0]
           - ocn.cn_objective_and_gradient(g, u0 - eps * du0, uo, dt, steps)[0]) / (2 * eps)
     assert abs(fd - np.sum(grad * du0)) < 1e-7 * abs(fd)
+
+
+@pytest.mark.parametrize("N,tol", [(4, 2e-2), (6, 1e-3), (8, 1e-5)])
+def test_frozen_advection_sweep_converges_to_advection_diffusion_solution(N, tol):
+    """Sec. 6.1 convergence study: with the advection frozen at a constant speed a,
+    du/dt = J(a) u is u_t + a u_x = nu u_xx, whose solution translates and damps
+    each Fourier mode (closed form in inputs.advection_diffusion_1d)."""
+    nu, a, T = 1e-3, 0.1, 0.05
+    g = Grid(1, 8, N, nu, L=1.0)
+    x = g.coords()
+    c = inputs.advection_diffusion_coefs(5)
+    A = np.full((1, g.G), a)
+    steps = 100
+    uT, _ = ork.rk_forward(lambda u: g.jac(A, u), inputs.advection_diffusion_1d(x, 0.0, c, nu, a), T / steps,
+                           steps, "rk4")
+    ref = inputs.advection_diffusion_1d(x, T, c, nu, a)
+    assert np.max(np.abs(uT - ref)) < tol
+    # a wrong sign of the advection would move the modes the other way
+    assert np.max(np.abs(ref - inputs.advection_diffusion_1d(x, T, c, nu, -a))) > 0.1
