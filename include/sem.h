@@ -73,6 +73,10 @@ typedef struct sem_ctx* sem_t;
 #define SEM_CKPT_STAGES    1  /* store every stage value of every step: adjoint = s J^T per step */
 #define SEM_CKPT_STATES    2  /* store every step's state; recompute its stages in the adjoint */
 #define SEM_CKPT_BINOMIAL  3  /* ckpt_slots state slots, revolve-optimal recomputation */
+#define SEM_CKPT_TWO_LEVEL 4  /* every step's state: as many as ckpt_budget_bytes allow
+                                 (less a 3-state staging ring) in device memory, the rest in
+                                 pinned host memory (sem_set_host_tier); AUTO picks it after
+                                 STATES when a host budget is set */
 
 typedef struct {
     int    dim;                /* 1, 2 or 3 */
@@ -180,6 +184,23 @@ int sem_sweep_stats(sem_t h, long long* out3);
  * a == NULL returns the handle to Burgers.  Either call discards the recorded
  * forward sweep and any recorded gradient graph. */
 int sem_set_advection(sem_t h, const double* a, void* stream);
+
+/* Second level of the trajectory store (Sec. 5.4: the paper's checkpoints may
+ * live in RAM or on disk).  host_bytes > 0 lets SEM_CKPT_TWO_LEVEL (and AUTO, when
+ * every step's state does not fit the device budget) keep states in up to
+ * host_bytes of pinned host memory, allocated at the next forward sweep that needs
+ * them.  The forward sweep copies each host-tier state from a device staging slot
+ * on a second stream while the following steps compute; the adjoint sweep loads
+ * them back up to three steps ahead.  Results are bitwise equal to
+ * SEM_CKPT_STATES.  Gradient evaluations that use the host tier run without a
+ * CUDA graph.  0 releases the host buffer (after synchronising the device).
+ * Returns SEM_ERR_OOM from the sweep if the states do not fit both levels. */
+int sem_set_host_tier(sem_t h, size_t host_bytes);
+
+/* Storage used by the last forward sweep: out4[0] its SEM_CKPT_* mode (0 when none
+ * was recorded or the sweep was linear), out4[1] vectors held on the device,
+ * out4[2] states held in host memory, out4[3] binomial slots.  Host-only. */
+int sem_trajectory_info(sem_t h, long long* out4);
 
 /* Settings of the SEM_CN solves (Sec. 6.3 names the scheme; the solver is this
  * library's): Newton stops when |delta| <= newton_rtol max(|u_{n+1}|, 1) (2-norms);

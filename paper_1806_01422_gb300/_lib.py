@@ -19,7 +19,7 @@ SEM_ERR_CUDA = -6
 
 SEM_RK4, SEM_SSPRK3, SEM_EULER, SEM_CN = 0, 1, 2, 3
 SEM_PREC_FP64, SEM_PREC_FP32_BULK = 0, 1
-SEM_CKPT_AUTO, SEM_CKPT_STAGES, SEM_CKPT_STATES, SEM_CKPT_BINOMIAL = 0, 1, 2, 3
+SEM_CKPT_AUTO, SEM_CKPT_STAGES, SEM_CKPT_STATES, SEM_CKPT_BINOMIAL, SEM_CKPT_TWO_LEVEL = 0, 1, 2, 3, 4
 
 
 class sem_opts(ctypes.Structure):
@@ -56,6 +56,8 @@ _SIGS = {
     "sem_sweep_stats": (_I, [_H, ctypes.POINTER(ctypes.c_longlong)]),
     "sem_set_solver": (_I, [_H, _D, _D, _I, _I]),
     "sem_set_advection": (_I, [_H, _P, _P]),
+    "sem_set_host_tier": (_I, [_H, ctypes.c_size_t]),
+    "sem_trajectory_info": (_I, [_H, ctypes.POINTER(ctypes.c_longlong)]),
     "sem_solver_stats": (_I, [_H, ctypes.POINTER(ctypes.c_longlong)]),
     "sem_profile": (_I, [_H, _I]),
     "sem_profile_read": (_I, [_H, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), _I]),

@@ -15,7 +15,7 @@ from . import _lib as L
 SCHEMES = {"rk4": L.SEM_RK4, "ssprk3": L.SEM_SSPRK3, "euler": L.SEM_EULER, "cn": L.SEM_CN}
 PRECISIONS = {"fp64": L.SEM_PREC_FP64, "fp32_bulk": L.SEM_PREC_FP32_BULK}
 CKPT = {"auto": L.SEM_CKPT_AUTO, "stages": L.SEM_CKPT_STAGES, "states": L.SEM_CKPT_STATES,
-        "binomial": L.SEM_CKPT_BINOMIAL}
+        "binomial": L.SEM_CKPT_BINOMIAL, "two_level": L.SEM_CKPT_TWO_LEVEL}
 
 
 def _stream(device):
@@ -160,6 +160,17 @@ class Sem:
         a = self._dev(a, "a")
         L.check(L.lib().sem_set_advection(self._h, self._p(a), _stream(self.device)))
         self._frozen = a   # kept alive until the copy on the stream has run
+
+    def set_host_tier(self, host_bytes):
+        """Pinned host memory for the second level of the trajectory store (sem_set_host_tier)."""
+        L.check(L.lib().sem_set_host_tier(self._h, int(host_bytes)))
+
+    def trajectory_info(self):
+        out = (ctypes.c_longlong * 4)()
+        L.check(L.lib().sem_trajectory_info(self._h, out))
+        modes = {v: k for k, v in CKPT.items()}
+        return {"mode": modes.get(out[0], None) if out[0] else None, "device": out[1], "host": out[2],
+                "slots": out[3]}
 
     def set_solver(self, newton_rtol=1e-12, krylov_rtol=1e-12, krylov_m=30, krylov_maxit=2000):
         """Newton / GMRES settings of the Crank-Nicolson scheme (sem_set_solver)."""

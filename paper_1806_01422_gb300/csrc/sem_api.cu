@@ -139,6 +139,13 @@ struct sem_ctx {
     int f_scheme = 0, f_nsteps = 0, f_mode = 0, f_slots = 0;
     double f_dt = 0;
     std::vector<int> f_ckpt;
+    // two-level trajectory store: states [0, f_ndev) in HBM, [f_ndev, nsteps) in pinned host memory
+    size_t host_budget = 0;
+    double* host_traj = nullptr;
+    size_t host_vectors = 0;
+    int f_ndev = 0;
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t ev_comp[3] = {}, ev_copy[3] = {}, ev_load[3] = {}, ev_done[3] = {};
     long long st[3] = {0, 0, 0};  // forward F applies, adjoint F applies, adjoint J^T applies
     // CUDA graph of one gradient evaluation (sem_set_graph), keyed on its arguments
     bool graph_on = false;
@@ -181,6 +188,8 @@ namespace {
 // work vector roles inside sem_ctx::vecs
 // internal storage mode of a linear (frozen-advection) sweep: nothing stored
 constexpr int MODE_LINEAR = 100;
+// staging ring (device state slots) between the compute stream and host memory
+constexpr int TWO_LEVEL_RING = 3;
 
 enum { V_K0 = 0, V_STAGE0 = 4, V_CUR0 = 7, V_CUR1 = 8, V_NU = 9, V_UN = 10, V_LAM = 11, NVEC = 12 };
 
@@ -214,7 +223,7 @@ int validate(const sem_opts* o) {
     if (!std::isfinite(o->L)) return fail(SEM_ERR_ARG, "L must be finite");
     if (o->precision != SEM_PREC_FP64 && o->precision != SEM_PREC_FP32_BULK)
         return fail(SEM_ERR_ARG, "unknown precision %d", o->precision);
-    if (o->ckpt_mode < SEM_CKPT_AUTO || o->ckpt_mode > SEM_CKPT_BINOMIAL)
+    if (o->ckpt_mode < SEM_CKPT_AUTO || o->ckpt_mode > SEM_CKPT_TWO_LEVEL)
         return fail(SEM_ERR_ARG, "unknown checkpoint mode %d", o->ckpt_mode);
     if (o->ckpt_mode == SEM_CKPT_BINOMIAL && o->ckpt_slots < 1)
         return fail(SEM_ERR_ARG, "binomial checkpointing needs ckpt_slots >= 1");
@@ -564,6 +573,19 @@ int alloc_traj(sem_t h, size_t nvec) {
     return SEM_OK;
 }
 
+// Device budget of the trajectory (explicit, or free memory less 4 GiB of headroom).
+size_t device_budget(sem_t h) {
+    if (h->ckpt_budget) return h->ckpt_budget;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        fr = 0;
+    }
+    fr += h->traj ? h->traj_vectors * vec_bytes(h) : 0;
+    const size_t headroom = (size_t)4 << 30;
+    return fr > headroom ? fr - headroom : fr / 2;
+}
+
 // Storage mode for a sweep of nsteps steps of an s-stage scheme.
 int choose_mode(sem_t h, int s, int nsteps, int& mode, int& slots) {
     if (h->fixed_mode >= 0) {
@@ -574,27 +596,49 @@ int choose_mode(sem_t h, int s, int nsteps, int& mode, int& slots) {
     mode = h->ckpt_mode;
     slots = h->ckpt_slots;
     if (mode != SEM_CKPT_AUTO) return SEM_OK;
-    size_t budget = h->ckpt_budget;
-    if (!budget) {
-        // no explicit budget: the free device memory (plus the trajectory buffer
-        // this handle would release) minus 4 GiB of headroom for other users
-        size_t fr = 0, tot = 0;
-        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
-            cudaGetLastError();
-            fr = 0;
-        }
-        fr += h->traj ? h->traj_vectors * vec_bytes(h) : 0;
-        const size_t headroom = (size_t)4 << 30;
-        budget = fr > headroom ? fr - headroom : fr / 2;
-    }
+    // without an explicit budget: the free device memory (plus the trajectory buffer
+    // this handle would release) minus 4 GiB of headroom for other users
+    const size_t budget = device_budget(h);
     const size_t v = vec_bytes(h);
     if ((size_t)nsteps * s * v <= budget) mode = SEM_CKPT_STAGES;
     else if ((size_t)nsteps * v <= budget) mode = SEM_CKPT_STATES;
+    else if (h->host_budget && budget >= TWO_LEVEL_RING * v &&
+             (size_t)nsteps * v <= budget - TWO_LEVEL_RING * v + h->host_budget)
+        mode = SEM_CKPT_TWO_LEVEL;
     else {
         mode = SEM_CKPT_BINOMIAL;
         slots = (int)(budget / v);
         if (slots < 1) return fail(SEM_ERR_OOM, "not even one checkpoint slot fits in %zu bytes", budget);
     }
+    return SEM_OK;
+}
+
+// Two-level store: the copy stream, its events and the pinned host buffer for nhost states.
+int two_level_setup(sem_t h, size_t nhost) {
+    if (!h->cstream) SEM_CK(cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking));
+    for (int k = 0; k < TWO_LEVEL_RING; ++k) {
+        if (!h->ev_comp[k]) SEM_CK(cudaEventCreateWithFlags(&h->ev_comp[k], cudaEventDisableTiming));
+        if (!h->ev_copy[k]) SEM_CK(cudaEventCreateWithFlags(&h->ev_copy[k], cudaEventDisableTiming));
+        if (!h->ev_load[k]) SEM_CK(cudaEventCreateWithFlags(&h->ev_load[k], cudaEventDisableTiming));
+        if (!h->ev_done[k]) SEM_CK(cudaEventCreateWithFlags(&h->ev_done[k], cudaEventDisableTiming));
+    }
+    if (nhost * vec_bytes(h) > h->host_budget)
+        return fail(SEM_ERR_OOM, "%zu host states exceed the host budget of %zu bytes", nhost, h->host_budget);
+    if (h->host_traj && h->host_vectors >= nhost) return SEM_OK;
+    if (h->host_traj) {
+        SEM_CK(cudaStreamSynchronize(h->cstream));
+        cudaFreeHost(h->host_traj);
+        h->host_traj = nullptr;
+        h->host_vectors = 0;
+    }
+    cudaError_t e = cudaMallocHost((void**)&h->host_traj, nhost * vec_bytes(h));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->host_traj = nullptr;
+        return fail(SEM_ERR_OOM, "pinned host trajectory of %zu bytes: %s", nhost * vec_bytes(h),
+                    cudaGetErrorString(e));
+    }
+    h->host_vectors = nhost;
     return SEM_OK;
 }
 
@@ -626,7 +670,17 @@ int forward_impl(sem_t h, int scheme, double dt, int nsteps, const double* u0, d
     SEM_TRY(choose_mode(h, T.s, nsteps, mode, slots));
     if (mode == SEM_CKPT_BINOMIAL && slots > nsteps) slots = nsteps;
     if (h->frozen) mode = MODE_LINEAR;   // the adjoint needs no stage values
-    const size_t nvec = mode == SEM_CKPT_STAGES ? (size_t)nsteps * T.s : (mode == SEM_CKPT_STATES ? (size_t)nsteps : (size_t)slots);
+    int ndev = nsteps;
+    if (mode == SEM_CKPT_TWO_LEVEL) {
+        if (!h->host_budget) return fail(SEM_ERR_ARG, "two-level storage needs a host budget (sem_set_host_tier)");
+        const size_t fit = device_budget(h) / vec_bytes(h);
+        if (fit < (size_t)TWO_LEVEL_RING) return fail(SEM_ERR_OOM, "the device budget holds fewer than 3 states");
+        ndev = (int)std::min<size_t>((size_t)nsteps, fit - TWO_LEVEL_RING);
+        SEM_TRY(two_level_setup(h, (size_t)(nsteps - ndev)));
+    }
+    const size_t nvec = mode == SEM_CKPT_STAGES ? (size_t)nsteps * T.s
+                        : mode == SEM_CKPT_STATES ? (size_t)nsteps
+                        : mode == SEM_CKPT_TWO_LEVEL ? (size_t)ndev + TWO_LEVEL_RING : (size_t)slots;
     if (mode != MODE_LINEAR) SEM_TRY(alloc_traj(h, nvec));
     h->have_fwd = false;
     const size_t vb = vec_bytes(h);
@@ -669,6 +723,41 @@ int forward_impl(sem_t h, int scheme, double dt, int nsteps, const double* u0, d
             double* next = n + 1 < nsteps ? h->traj + (size_t)(n + 1) * h->ndof : uT;
             SEM_TRY(rk_stages(h, T, dt, un, Yw, next, s, count));
         }
+    } else if (mode == SEM_CKPT_TWO_LEVEL) {
+        // states n < ndev in HBM; later ones through the staging ring to pinned host memory,
+        // copied on the copy stream while the next steps compute
+        auto slot = [&](int n) -> double* {
+            return h->traj + (size_t)(n < ndev ? n : ndev + n % TWO_LEVEL_RING) * h->ndof;
+        };
+        bool pending[TWO_LEVEL_RING] = {false, false, false};
+        auto offload = [&](int n) -> int {
+            const int k = n % TWO_LEVEL_RING;
+            SEM_CK(cudaEventRecord(h->ev_comp[k], s));
+            SEM_CK(cudaStreamWaitEvent(h->cstream, h->ev_comp[k], 0));
+            SEM_CK(cudaMemcpyAsync(h->host_traj + (size_t)(n - ndev) * h->ndof, slot(n), vb, cudaMemcpyDeviceToHost,
+                                   h->cstream));
+            SEM_CK(cudaEventRecord(h->ev_copy[k], h->cstream));
+            pending[k] = true;
+            return SEM_OK;
+        };
+        auto claim = [&](int n) -> int {   // the ring slot of state n may be overwritten
+            const int k = n % TWO_LEVEL_RING;
+            if (pending[k]) SEM_CK(cudaStreamWaitEvent(s, h->ev_copy[k], 0));
+            pending[k] = false;
+            return SEM_OK;
+        };
+        if (ndev == 0) SEM_TRY(claim(0));
+        SEM_TRY(put_u0(slot(0)));
+        if (ndev == 0) SEM_TRY(offload(0));
+        for (int n = 0; n < nsteps; ++n) {
+            const bool last = n + 1 == nsteps;
+            const bool to_host = !last && n + 1 >= ndev;
+            if (to_host) SEM_TRY(claim(n + 1));
+            SEM_TRY(rk_stages(h, T, dt, slot(n), Yw, last ? uT : slot(n + 1), s, count));
+            if (to_host) SEM_TRY(offload(n + 1));
+        }
+        for (int k = 0; k < TWO_LEVEL_RING; ++k)
+            if (pending[k]) SEM_CK(cudaStreamWaitEvent(s, h->ev_copy[k], 0));
     } else {
         semh::CkptPlanner P(nsteps, slots);
         ckpt = P.forward_checkpoints(nsteps, slots);
@@ -695,6 +784,7 @@ int forward_impl(sem_t h, int scheme, double dt, int nsteps, const double* u0, d
     h->f_mode = mode;
     h->f_slots = slots;
     h->f_ckpt = ckpt;
+    h->f_ndev = mode == SEM_CKPT_TWO_LEVEL ? ndev : 0;
     h->st[0] = count;
     return SEM_OK;
 }
@@ -745,6 +835,37 @@ int adjoint_impl(sem_t h, const double* lamT, double* lam0, cudaStream_t s, bool
             SEM_TRY(rk_stages(h, T, dt, un, Yw, nullptr, s, nrhs));
             const double* Y[4] = {Yw[0], Yw[1], Yw[2], Yw[3]};
             SEM_TRY(rk_adjoint_step(h, T, dt, Y, lam0, s, njt));
+        }
+    } else if (h->f_mode == SEM_CKPT_TWO_LEVEL) {
+        // host states come back through the staging ring, loaded up to 3 steps ahead on the copy stream
+        const int ndev = h->f_ndev;
+        bool used[TWO_LEVEL_RING] = {false, false, false};
+        // the copy stream starts after everything the caller queued before this sweep on s
+        SEM_CK(cudaEventRecord(h->ev_comp[0], s));
+        SEM_CK(cudaStreamWaitEvent(h->cstream, h->ev_comp[0], 0));
+        auto ring = [&](int n) { return h->traj + (size_t)(ndev + n % TWO_LEVEL_RING) * h->ndof; };
+        auto load = [&](int n) -> int {
+            const int k = n % TWO_LEVEL_RING;
+            if (used[k]) SEM_CK(cudaStreamWaitEvent(h->cstream, h->ev_done[k], 0));
+            SEM_CK(cudaMemcpyAsync(ring(n), h->host_traj + (size_t)(n - ndev) * h->ndof, vb, cudaMemcpyHostToDevice,
+                                   h->cstream));
+            SEM_CK(cudaEventRecord(h->ev_load[k], h->cstream));
+            return SEM_OK;
+        };
+        for (int n = nsteps - 1; n >= std::max(ndev, nsteps - TWO_LEVEL_RING); --n) SEM_TRY(load(n));
+        for (int n = nsteps - 1; n >= 0; --n) {
+            const bool host = n >= ndev;
+            double* un = host ? ring(n) : h->traj + (size_t)n * h->ndof;
+            if (host) SEM_CK(cudaStreamWaitEvent(s, h->ev_load[n % TWO_LEVEL_RING], 0));
+            Yw[0] = un;
+            SEM_TRY(rk_stages(h, T, dt, un, Yw, nullptr, s, nrhs));
+            const double* Y[4] = {Yw[0], Yw[1], Yw[2], Yw[3]};
+            SEM_TRY(rk_adjoint_step(h, T, dt, Y, lam0, s, njt));   // reads u_n as stage 0
+            if (host) {
+                SEM_CK(cudaEventRecord(h->ev_done[n % TWO_LEVEL_RING], s));
+                used[n % TWO_LEVEL_RING] = true;
+                if (n - TWO_LEVEL_RING >= ndev) SEM_TRY(load(n - TWO_LEVEL_RING));
+            }
         }
     } else {
         semh::CkptPlanner P(nsteps, h->f_slots);
@@ -1269,6 +1390,14 @@ void sem_destroy(sem_t h) {
     cudaFree(h->kpart);
     cudaFree(h->kscal);
     cudaFree(h->frozen);
+    if (h->host_traj) cudaFreeHost(h->host_traj);
+    for (int k = 0; k < 3; ++k) {
+        if (h->ev_comp[k]) cudaEventDestroy(h->ev_comp[k]);
+        if (h->ev_copy[k]) cudaEventDestroy(h->ev_copy[k]);
+        if (h->ev_load[k]) cudaEventDestroy(h->ev_load[k]);
+        if (h->ev_done[k]) cudaEventDestroy(h->ev_done[k]);
+    }
+    if (h->cstream) cudaStreamDestroy(h->cstream);
     if (h->batch) {
         BatchHost* b = h->batch;
         cudaFree(b->d_inst);
@@ -1444,8 +1573,16 @@ int sem_objective_grad(sem_t h, int scheme, double dt, int nsteps, const double*
     if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 1) return fail(SEM_ERR_ARG, "dt > 0 and nsteps >= 1");
     SEM_TRY(ensure_workspace(h));
     cudaStream_t s = (cudaStream_t)stream;
-    // the implicit scheme synchronises with the host inside its solves: never captured
-    const bool graph = h->graph_on && scheme != SEM_CN;
+    // the implicit scheme synchronises with the host inside its solves, and the two-level
+    // store runs a second stream: neither is captured
+    bool graph = h->graph_on && scheme != SEM_CN;
+    if (graph) {
+        Tableau T;
+        int mode, slots;
+        if (!tableau_of(scheme, T)) return fail(SEM_ERR_ARG, "unknown time scheme %d", scheme);
+        SEM_TRY(choose_mode(h, T.s, nsteps, mode, slots));
+        if (mode == SEM_CKPT_TWO_LEVEL && !h->frozen) graph = false;
+    }
     if (graph) SEM_TRY(objective_grad_graph(h, scheme, dt, nsteps, u0, uo, grad, s));
     else SEM_TRY(objective_grad_launches(h, scheme, dt, nsteps, u0, uo, grad, s));
     unsigned f = 0;
@@ -1521,6 +1658,37 @@ int sem_set_advection(sem_t h, const double* a, void* stream) {
     } else {
         SEM_CK(cudaMemcpyAsync(h->frozen, a, vec_bytes(h), cudaMemcpyDeviceToDevice, s));
     }
+    return SEM_OK;
+}
+
+int sem_set_host_tier(sem_t h, size_t host_bytes) {
+    if (!h) return fail(SEM_ERR_ARG, "null handle");
+    if (h->host_traj && host_bytes < h->host_vectors * vec_bytes(h)) {
+        if (h->cstream) SEM_CK(cudaStreamSynchronize(h->cstream));
+        SEM_CK(cudaDeviceSynchronize());
+        cudaFreeHost(h->host_traj);
+        h->host_traj = nullptr;
+        h->host_vectors = 0;
+        if (h->f_mode == SEM_CKPT_TWO_LEVEL) h->have_fwd = false;
+    }
+    h->host_budget = host_bytes;
+    return SEM_OK;
+}
+
+int sem_trajectory_info(sem_t h, long long* out4) {
+    if (!h || !out4) return fail(SEM_ERR_ARG, "null handle or output");
+    out4[0] = out4[1] = out4[2] = out4[3] = 0;
+    if (!h->have_fwd || h->f_mode == MODE_LINEAR) return SEM_OK;
+    Tableau T;
+    const int stages = h->f_scheme == SEM_CN ? 1 : (tableau_of(h->f_scheme, T) ? T.s : 1);
+    out4[0] = h->f_mode;
+    if (h->f_scheme == SEM_CN) out4[1] = h->f_nsteps + 1;
+    else if (h->f_mode == SEM_CKPT_STAGES) out4[1] = (long long)h->f_nsteps * stages;
+    else if (h->f_mode == SEM_CKPT_STATES) out4[1] = h->f_nsteps;
+    else if (h->f_mode == SEM_CKPT_TWO_LEVEL) {
+        out4[1] = h->f_ndev;
+        out4[2] = h->f_nsteps - h->f_ndev;
+    } else out4[3] = h->f_slots;
     return SEM_OK;
 }
 
