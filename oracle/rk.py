@@ -35,6 +35,12 @@ TABLEAUX = {
                np.array([1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0])),
     # forward Euler, the case worked out in Sec. 4.1
     "euler": (np.array([[0.0]]), np.array([1.0])),
+    # Bogacki-Shampine third-order method (the solution part of the 3(2) pair; its
+    # fourth, first-same-as-last stage only serves the error estimate, oracle/adapt.py)
+    "bs3": (np.array([[0.0, 0.0, 0.0],
+                      [0.5, 0.0, 0.0],
+                      [0.0, 0.75, 0.0]]),
+            np.array([2.0 / 9.0, 1.0 / 3.0, 4.0 / 9.0])),
 }
 
 

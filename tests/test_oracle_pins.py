@@ -16,6 +16,7 @@ from oracle.gll import gll
 from oracle.sem import Grid
 from oracle import rk as ork
 from oracle.checkpoint import optimal_advances, checkpointed_gradient_lam0
+from oracle import adapt as oad
 from paper_1806_01422_gb300 import inputs
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -235,7 +236,7 @@ def test_objective_closed_forms():
 
 
 # ----------------------------------------------------- RK sweeps (Sec. 4.1)
-@pytest.mark.parametrize("scheme,order", [("rk4", 4), ("ssprk3", 3), ("euler", 1)])
+@pytest.mark.parametrize("scheme,order", [("rk4", 4), ("ssprk3", 3), ("euler", 1), ("bs3", 3)])
 def test_rk_step_is_taylor_polynomial_on_linear_problems(scheme, order):
     rng = np.random.default_rng(4)
     A = rng.standard_normal((6, 6))
@@ -400,3 +401,43 @@ def test_frozen_advection_sweep_converges_to_advection_diffusion_solution(N, tol
     assert np.max(np.abs(uT - ref)) < tol
     # a wrong sign of the advection would move the modes the other way
     assert np.max(np.abs(ref - inputs.advection_diffusion_1d(x, T, c, nu, -a))) > 0.1
+
+
+# ----------------------------------------------------- adaptive stepping (Sec. 5.1)
+def test_bs3_embedded_pair_orders():
+    """For u' = a u (z = a dt) the stages are k1 = a u, k2 = a (1 + z/2) u,
+    k3 = a (1 + 3z/4 + 3z^2/8) u and k4 = a R(z) u with R = 1 + z + z^2/2 + z^3/6, so
+    the companion solution is (1 + z + z^2/2 + 3z^3/16 + z^4/48) u and the error
+    estimate E = u_{n+1} - uhat_{n+1} is exactly -(z^3 + z^4)/48 u: O(dt^3), the
+    local error of the second-order member."""
+    a = -1.3
+    for dt in (1e-2, 5e-3, 0.3):
+        _, _, E = oad.bs3_step(lambda y: a * y, np.array([1.0]), dt)
+        z = a * dt
+        assert abs(E[0] + (z ** 3 + z ** 4) / 48.0) < 1e-15 * max(1.0, abs(z) ** 3)
+
+
+def test_adaptive_sweep_hits_the_horizon_and_follows_the_tolerance():
+    a = -2.0
+    errs = []
+    for tol in (1e-5, 1e-8):
+        u, traj, dts, rej = oad.adaptive_forward(lambda y: a * y, np.array([1.0]), 1.0, 0.3, tol, tol)
+        assert abs(sum(dts) - 1.0) < 1e-13
+        errs.append(abs(u[0] - np.exp(a)))
+    assert errs[1] < errs[0] / 100
+    # a large first step is rejected and shrunk
+    _, _, dts, rej = oad.adaptive_forward(lambda y: a * y, np.array([1.0]), 1.0, 0.9, 1e-8, 1e-8)
+    assert rej >= 1 and dts[0] < 0.9
+
+
+def test_adaptive_adjoint_is_the_transpose_of_its_tangent():
+    g = Grid(1, 6, 5, 0.02)
+    rng = np.random.default_rng(21)
+    u0 = inputs.field_1d(g.coords(), 1)
+    _, traj, dts, _ = oad.adaptive_forward(g.rhs, u0, 0.2, 0.01, 1e-6, 1e-6)
+    assert len(set(dts)) > 2                     # the step really varies
+    du0, lamT = rng.standard_normal((2,) + u0.shape)
+    duN = oad.tangent_variable(g.jac, traj, du0, dts)
+    lam0 = oad.adjoint_variable(g.jacT, traj, lamT, dts)
+    lhs, rhs = float(np.sum(lamT * duN)), float(np.sum(lam0 * du0))
+    assert abs(lhs - rhs) < 1e-12 * max(abs(lhs), 1.0)
