@@ -33,9 +33,12 @@ WORKLOADS = {
                     "nu=1e-3, SSP-RK3 dt=2e-4 x 2000 steps, all stages stored; one gradient evaluation per step",
                data="synthetic: seeded 16-mode Fourier fields (|k|_inf <= 8, amplitude ~|k|^-2, max|u0| = 1) "
                     "for u0 (seed 1) and u_obs (seed 2)"),
-    "3d": dict(dim=3, E=32, N=7, nu=5e-4, scheme="rk4", dt=2.5e-4, nsteps=1000, ckpt="binomial", slots=20,
+    # the 3D horizons stop before the fields steepen past what the grid resolves: at these
+    # viscosities the discrete solution (FP64 and FP32 alike) diverges near step 450 (N=7)
+    # and step 350 (N=15)
+    "3d": dict(dim=3, E=32, N=7, nu=5e-4, scheme="rk4", dt=2.5e-4, nsteps=300, ckpt="binomial", slots=20,
                desc="3D vector viscous Burgers, periodic [0,1]^3, 32^3 hexes, N=7 (33,718,272 unknowns), "
-                    "nu=5e-4, RK4 dt=2.5e-4 x 1000 steps, binomial checkpointing with 20 slots",
+                    "nu=5e-4, RK4 dt=2.5e-4 x 300 steps (T=0.075), binomial checkpointing with 20 slots",
                data="synthetic: seeded random-phase fields, spectrum ~k^-5/3 cut at |k| = 16, max|u0| = 1"),
     "batch": dict(dim=2, E=None, N=None, nu=1e-3, scheme="rk4", dt=1.5e-4, nsteps=300, ckpt="states", slots=0,
                   count=256,
@@ -44,9 +47,9 @@ WORKLOADS = {
                        "one persistent launch per operator pass, every step's state stored (stages recomputed); one "
                        "batched gradient evaluation per step (256 instance gradients)",
                   data="synthetic: per instance k seeded 16-mode Fourier fields (seeds 1000+2k, 1001+2k)"),
-    "3d15": dict(dim=3, E=16, N=15, nu=2e-4, scheme="rk4", dt=2e-4, nsteps=400, ckpt="states", slots=0,
+    "3d15": dict(dim=3, E=16, N=15, nu=2e-4, scheme="rk4", dt=2e-4, nsteps=300, ckpt="states", slots=0,
                  desc="3D vector viscous Burgers, periodic [0,1]^3, 16^3 hexes, N=15 (41,472,000 unknowns), "
-                      "nu=2e-4, RK4 dt=2e-4 x 400 steps, every step's state stored (stages recomputed)",
+                      "nu=2e-4, RK4 dt=2e-4 x 300 steps (T=0.06), every step's state stored (stages recomputed)",
                  data="synthetic: seeded random-phase fields, spectrum ~k^-5/3 cut at |k| = 16, max|u0| = 1"),
     "2dcn": dict(dim=2, E=64, N=7, nu=1e-3, scheme="cn", dt=2e-3, nsteps=200, ckpt="states", slots=0,
                  desc="2D vector viscous Burgers, periodic [0,1]^2, 64x64 quads, N=7 (401,408 unknowns), "
@@ -65,6 +68,8 @@ WORKLOADS = {
 # FMA lanes per SM.
 PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Double-float element arithmetic: a compensated multiply-add costs 13 FP32 operations.
+PEAK_DF_TFLOPS = 152 * 128 * 2.07e9 / 13 * 2 / 1e12
 
 # DRAM traffic per launch (bytes) of the dominant kernel from one ncu capture,
 # valid only while the kernel sources hash to the recorded value.
@@ -365,10 +370,14 @@ def gpu_arm(args, world, rank, local):
     else:
         flops = sum(algorithmic_flops_per_element(dom, w["dim"], N + 1) * E ** w["dim"] for E, N in shapes)
         achieved = flops / avg_s / 1e12
-        peak = PEAK_FP32_TFLOPS if fp32 else PEAK_FP64_TFLOPS
+        dfk = args.precision == "fp64_df"
+        peak = PEAK_FP32_TFLOPS if fp32 else (PEAK_DF_TFLOPS if dfk else PEAK_FP64_TFLOPS)
+        ctype = "float" if fp32 else ("semk::dfa::dfloat" if dfk else "double")
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "kernel": kname or "%s%d_kernel<%s,%d>" % (names[dom], w["dim"], "float" if fp32 else "double",
-                                                         w["N"] + 1)}
+                "kernel": kname or "%s%d_kernel<%s,%d>" % (names[dom], w["dim"], ctype, w["N"] + 1)}
+        if dfk:
+            roof["peak_note"] = ("double-float multiply-add rate of the FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz "
+                                 "/ 13 FP32 operations per multiply-add, x 2 flop")
     key = "%s@%s@%s" % (roof["kernel"], args.workload, args.precision)
     tr = TRAFFIC.get(key)
     tr_ok = tr and tr["src"] == kernel_src_hash("assemble" if dom == "assemble" else "elem")
@@ -391,7 +400,8 @@ def gpu_arm(args, world, rank, local):
                                   "binomial": w["slots"]}.get(w["ckpt"], nsteps)
     out = {"metric": METRIC, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1e3, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": w["data"],
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else ("f32x2 (double-float element kernels; f64 states and reductions)"
+                                                if args.precision == "fp64_df" else "f64"), "data": w["data"],
            "config": {"workload": w["desc"], "dim": w["dim"], "E": w["E"], "N": w["N"], "unknowns": s.ndof,
                       "instances": units,
                       "scheme": scheme, "dt": dt, "rk_steps": nsteps, "trajectory": w["ckpt"],
@@ -416,7 +426,35 @@ def gpu_arm(args, world, rank, local):
                       "h2d_bytes_per_step": 2 * s.ndof * 8, "d2h_bytes_per_step": s.ndof * 8 + 8}
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
+    if rank == 0 and args.lbfgs and args.workload != "batch":
+        out["lbfgs"] = lbfgs_run(s, w, args.lbfgs, dev)
     return out if rank == 0 else None
+
+
+def lbfgs_run(s, w, iters, dev):
+    """The optimisation loop of Fig. 1: recover the initial condition that produced u_obs.
+
+    u_obs is the final state of the forward sweep from the seed-2 field; the search starts
+    from the seed-1 field.  Outside the timed region.
+    """
+    import torch
+    from paper_1806_01422_gb300 import inputs
+    from paper_1806_01422_gb300.inverse import recover_initial_condition
+    x = s.coords()
+    u_true = torch.from_numpy(inputs.workload_field(w["dim"], x, inputs.SEED_UOBS)).to(dev)
+    u_init = torch.from_numpy(inputs.workload_field(w["dim"], x, inputs.SEED_U0)).to(dev)
+    s.use_graph(False)   # every evaluation point is a new tensor: stream launches, no re-recording
+    u_obs = s.rk_forward(u_true, w["dt"], w["nsteps"], w["scheme"]).clone()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    est, hist = recover_initial_condition(s, u_obs, u_init, w["dt"], w["nsteps"], w["scheme"], iters=iters)
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    rel = lambda a: float((a - u_true).norm() / u_true.norm())
+    return {"iterations": hist[-1][0], "gradient_evals": hist[-1][3], "seconds": t1 - t0,
+            "J_first": hist[0][1], "J_last": hist[-1][1], "grad_norm_first": hist[0][2], "grad_norm_last": hist[-1][2],
+            "u0_rel_error_first": rel(u_init), "u0_rel_error_last": rel(est),
+            "J_history": [h[1] for h in hist]}
 
 
 def extras(s, u0, uo, w, dev):
@@ -455,15 +493,13 @@ def extras(s, u0, uo, w, dev):
             "forward_ms": fwd, "adjoint_ms": adj, "adjoint_forward_ratio": adj / fwd}
 
 
-def order_sweep(precisions=("fp64", "fp32_bulk"), target=34e6, reps=10):
+def order_sweep(precisions=("fp64", "fp64_df", "fp32_bulk"), target=34e6, reps=10):
     """Standalone F(u) and J^T v throughput over orders N at about `target` 3D unknowns."""
     import torch
     from paper_1806_01422_gb300 import Sem, inputs
     rows = []
     for prec in precisions:
-        for N in (3, 5, 7, 9, 11, 15):
-            if prec == "fp64" and N > 11:
-                continue
+        for N in (3, 5, 7, 9, 11, 13, 15):
             E = max(2, int(round((target / 3) ** (1 / 3) / N)))
             s = Sem(3, E, N, 5e-4, precision=prec)
             x = s.coords()
@@ -513,13 +549,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk", "fp64_df"])
     ap.add_argument("--hbm-peak", type=float, default=None, help="GB/s; default: MEASURED_PEAKS.json")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--oracle-rk-steps", type=int, default=10)
     ap.add_argument("--rk-steps", type=int, default=None,
                     help="override the workload's RK step count (profiling runs only; not a bench number)")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--lbfgs", type=int, default=0, metavar="K",
+                    help="after the timed region, run K L-BFGS iterations recovering u0 (single-instance workloads)")
     ap.add_argument("--profile-every", type=int, default=16, help="time one launch in this many per kernel kind")
     ap.add_argument("--no-graph", action="store_true", help="launch on the stream instead of replaying a CUDA graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -54,6 +54,8 @@ typedef struct sem_ctx* sem_t;
 #define SEM_RK4      0  /* classic 4-stage, 4th order */
 #define SEM_SSPRK3   1  /* Shu-Osher SSP 3-stage, 3rd order */
 #define SEM_EULER    2  /* forward Euler (the case of Sec. 4.1) */
+#define SEM_BS3      4  /* Bogacki-Shampine 3-stage, 3rd order; with sem_set_adaptive the
+                           3(2) pair with adaptive step sizes */
 /* implicit scheme */
 #define SEM_CN       3  /* Crank-Nicolson (Sec. 6.3): u_{n+1} - u_n = dt/2 (F(u_n) + F(u_{n+1})),
                            Newton with matrix-free GMRES per step; FP64 single-instance
@@ -67,6 +69,13 @@ typedef struct sem_ctx* sem_t;
                                   the <= 2^d element contributions per node; FP64
                                   RK stage accumulation, objective and adjoint
                                   accumulation */
+#define SEM_PREC_FP64_DF    2  /* the FP64 form with its element kernels (contractions
+                                  and pointwise products) in double-float arithmetic
+                                  on the FP32 pipe: pairs of floats, about 48
+                                  significand bits, compensated dot products; inputs,
+                                  element results, assembly, states and every
+                                  reduction in FP64.  Results agree with the FP64 form
+                                  to about 1e-13 relative (the 1e-11 bound holds). */
 
 /* trajectory storage for the adjoint sweep (Sec. 5.3, Sec. 5.4) */
 #define SEM_CKPT_AUTO      0  /* STAGES if it fits ckpt_budget_bytes, else STATES, else BINOMIAL */
@@ -184,6 +193,28 @@ int sem_sweep_stats(sem_t h, long long* out3);
  * a == NULL returns the handle to Burgers.  Either call discards the recorded
  * forward sweep and any recorded gradient graph. */
 int sem_set_advection(sem_t h, const double* a, void* stream);
+
+/* Adaptive step sizes (Sec. 5.1: the step follows an estimate of the local
+ * truncation error, weighted by absolute and relative tolerances).  With atol > 0
+ * or rtol > 0, sweeps with scheme SEM_BS3 (sem_rk_forward, sem_objective_grad)
+ * integrate over the horizon T = dt * nsteps starting from the trial step dt:
+ * each attempted step also evaluates F(u_{n+1}) for the second-order companion
+ * of the Bogacki-Shampine 3(2) pair; the error E = u_{n+1} - uhat_{n+1} is taken
+ * in the RMS norm weighted by 1 / (atol + rtol max(|u_n|, |u_{n+1}|)); a step is
+ * accepted when that norm is <= 1 and the next trial step is
+ * dt min(fmax, max(0.2, 0.9 err^(-1/3))), fmax = 5 (1 right after a rejection);
+ * the last step ends on T.  Each attempt synchronises the stream once to read the
+ * norm.  Every accepted state is kept on the device (growing the trajectory
+ * buffer, within ckpt_budget_bytes when set); sem_rk_adjoint differentiates the
+ * accepted steps with their sizes held fixed.  FP64 form only; never captured in
+ * a CUDA graph.  atol = rtol = 0 turns adaptivity off (SEM_BS3 then takes nsteps
+ * fixed steps). */
+int sem_set_adaptive(sem_t h, double atol, double rtol);
+
+/* Accepted and rejected steps of the last adaptive sweep, and the first
+ * min(cap, accepted) accepted step sizes in dts (may be NULL when cap = 0).
+ * Zeros when the last sweep was not adaptive.  Host-only. */
+int sem_adaptive_steps(sem_t h, int* accepted, int* rejected, double* dts, int cap);
 
 /* Second level of the trajectory store (Sec. 5.4: the paper's checkpoints may
  * live in RAM or on disk).  host_bytes > 0 lets SEM_CKPT_TWO_LEVEL (and AUTO, when

@@ -17,8 +17,8 @@ SEM_ERR_NONFINITE = -4
 SEM_ERR_STATE = -5
 SEM_ERR_CUDA = -6
 
-SEM_RK4, SEM_SSPRK3, SEM_EULER, SEM_CN = 0, 1, 2, 3
-SEM_PREC_FP64, SEM_PREC_FP32_BULK = 0, 1
+SEM_RK4, SEM_SSPRK3, SEM_EULER, SEM_CN, SEM_BS3 = 0, 1, 2, 3, 4
+SEM_PREC_FP64, SEM_PREC_FP32_BULK, SEM_PREC_FP64_DF = 0, 1, 2
 SEM_CKPT_AUTO, SEM_CKPT_STAGES, SEM_CKPT_STATES, SEM_CKPT_BINOMIAL, SEM_CKPT_TWO_LEVEL = 0, 1, 2, 3, 4
 
 
@@ -57,6 +57,8 @@ _SIGS = {
     "sem_set_solver": (_I, [_H, _D, _D, _I, _I]),
     "sem_set_advection": (_I, [_H, _P, _P]),
     "sem_set_host_tier": (_I, [_H, ctypes.c_size_t]),
+    "sem_set_adaptive": (_I, [_H, _D, _D]),
+    "sem_adaptive_steps": (_I, [_H, ctypes.POINTER(_I), ctypes.POINTER(_I), _P, _I]),
     "sem_trajectory_info": (_I, [_H, ctypes.POINTER(ctypes.c_longlong)]),
     "sem_solver_stats": (_I, [_H, ctypes.POINTER(ctypes.c_longlong)]),
     "sem_profile": (_I, [_H, _I]),

@@ -12,8 +12,8 @@ import torch
 
 from . import _lib as L
 
-SCHEMES = {"rk4": L.SEM_RK4, "ssprk3": L.SEM_SSPRK3, "euler": L.SEM_EULER, "cn": L.SEM_CN}
-PRECISIONS = {"fp64": L.SEM_PREC_FP64, "fp32_bulk": L.SEM_PREC_FP32_BULK}
+SCHEMES = {"rk4": L.SEM_RK4, "ssprk3": L.SEM_SSPRK3, "euler": L.SEM_EULER, "cn": L.SEM_CN, "bs3": L.SEM_BS3}
+PRECISIONS = {"fp64": L.SEM_PREC_FP64, "fp32_bulk": L.SEM_PREC_FP32_BULK, "fp64_df": L.SEM_PREC_FP64_DF}
 CKPT = {"auto": L.SEM_CKPT_AUTO, "stages": L.SEM_CKPT_STAGES, "states": L.SEM_CKPT_STATES,
         "binomial": L.SEM_CKPT_BINOMIAL, "two_level": L.SEM_CKPT_TWO_LEVEL}
 
@@ -160,6 +160,19 @@ class Sem:
         a = self._dev(a, "a")
         L.check(L.lib().sem_set_advection(self._h, self._p(a), _stream(self.device)))
         self._frozen = a   # kept alive until the copy on the stream has run
+
+    def set_adaptive(self, atol=0.0, rtol=0.0):
+        """Adaptive steps for scheme "bs3" (sem_set_adaptive); dt * nsteps is then the horizon."""
+        L.check(L.lib().sem_set_adaptive(self._h, float(atol), float(rtol)))
+
+    def adaptive_steps(self):
+        """(accepted step sizes as an ndarray, rejected count) of the last adaptive sweep."""
+        acc, rej = ctypes.c_int(), ctypes.c_int()
+        L.check(L.lib().sem_adaptive_steps(self._h, ctypes.byref(acc), ctypes.byref(rej), None, 0))
+        dts = np.empty(acc.value)
+        L.check(L.lib().sem_adaptive_steps(self._h, ctypes.byref(acc), ctypes.byref(rej),
+                                           dts.ctypes.data_as(ctypes.c_void_p), int(dts.size)))
+        return dts, rej.value
 
     def set_host_tier(self, host_bytes):
         """Pinned host memory for the second level of the trajectory store (sem_set_host_tier)."""

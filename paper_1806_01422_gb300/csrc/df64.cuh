@@ -117,4 +117,65 @@ __device__ __forceinline__ bool nonfinite_f(float v) {
     return (__float_as_uint(v) & 0x7f800000u) == 0x7f800000u;
 }
 
+// ---------------------------------------------------------------- double-float element arithmetic
+// Value type of the element kernels of the FP64-DF form: x = h + l in two floats
+// (about 48 significand bits), with the operators the element kernels use.  The
+// FP64 pipe of GB300 issues 2 lanes per SM and clock, the FP32 pipe 128; a
+// multiply-add below costs 13 FP32 operations, so it runs about 5 times faster
+// than a native FP64 FMA while its rounding error stays near 2^-48 relative to
+// the magnitudes summed (Ogita, Rump & Oishi, "Accurate sum and dot product",
+// SIAM J. Sci. Comput. 26 (2005): the compensated dot product, here with
+// double-float inputs).  Sums and products leave the pair unnormalised (|l| may
+// exceed half an ulp of h); its value h + l is what counts.  The operators live
+// in their own namespace so that argument-dependent lookup finds them and an
+// unqualified fma() on doubles still resolves to the CUDA math function.
+namespace dfa {
+
+struct dfloat {
+    float h, l;
+    dfloat() = default;
+    __host__ __device__ constexpr dfloat(float x) : h(x), l(0.f) {}
+    __host__ __device__ constexpr dfloat(float a, float b) : h(a), l(b) {}
+};
+
+__device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.h, -a.l); }
+
+// a + b: two-sum of the leading parts, trailing parts added in FP32
+__device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) {
+    const df s = df_two_sum(a.h, b.h);
+    return dfloat(s.hi, __fadd_rn(__fadd_rn(a.l, b.l), s.lo));
+}
+
+__device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return a + (-b); }
+
+// a * b: exact product of the leading parts (FMA), cross terms in FP32
+__device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) {
+    const float p = __fmul_rn(a.h, b.h);
+    const float e = __fmaf_rn(a.h, b.h, -p);
+    const float q = __fmaf_rn(a.h, b.l, __fmul_rn(a.l, b.h));
+    return dfloat(p, __fadd_rn(e, q));
+}
+
+// a * b + c: one step of the compensated dot product
+__device__ __forceinline__ dfloat fma(dfloat a, dfloat b, dfloat c) {
+    const float p = __fmul_rn(a.h, b.h);
+    const float e = __fmaf_rn(a.h, b.h, -p);
+    const float q = __fmaf_rn(a.h, b.l, __fmul_rn(a.l, b.h));
+    const df s = df_two_sum(c.h, p);
+    return dfloat(s.hi, __fadd_rn(c.l, __fadd_rn(__fadd_rn(e, q), s.lo)));
+}
+
+__device__ __forceinline__ dfloat& operator+=(dfloat& a, dfloat b) { return a = a + b; }
+__device__ __forceinline__ dfloat& operator-=(dfloat& a, dfloat b) { return a = a - b; }
+
+}  // namespace dfa
+
+using dfa::dfloat;
+
+// Host: the double-float nearest to a double (h rounded, l the rounded remainder).
+inline dfloat dfloat_of(double x) {
+    const float h = (float)x;
+    return dfloat(h, (float)(x - (double)h));
+}
+
 }  // namespace semk

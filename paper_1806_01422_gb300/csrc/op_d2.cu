@@ -1,5 +1,4 @@
-// Element-kernel instantiations for d = 2 (point counts n = 2..16; FP64 3D up to n = 16,
-// limited by the shared-memory tiles).
+// Element-kernel instantiations for d = 2 (point counts n = 2..16): FP64 and FP32.
 #include "op_launch.cuh"
 
 namespace semk {

@@ -64,7 +64,18 @@ __device__ __forceinline__ T inv_mult(int nb) {
 template <typename T>
 __device__ __forceinline__ T tile_value(const ElemArgs& a, const void* g, size_t i, bool scale_mult, int nb,
                                         float ref_hi, float ref_lo) {
-    if constexpr (sizeof(T) == 8) {
+    if constexpr (std::is_same<T, dfloat>::value) {
+        // double input split exactly enough (|x - h - l| <= 2^-47 |x|) with integer
+        // instructions; 1/k is a power of two
+        float h, l;
+        split_bits(__ldg((const double*)g + i), h, l);
+        if (scale_mult) {
+            const float s = inv_mult<float>(nb);
+            h *= s;
+            l *= s;
+        }
+        return dfloat(h, l);
+    } else if constexpr (sizeof(T) == 8) {
         const double x = __ldg((const double*)g + i);
         return scale_mult ? x * inv_mult<double>(nb) : x;
     } else {
@@ -205,7 +216,7 @@ __global__ void rhs3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
     for (int c = 0; c < 3; ++c) rU[c] = load3<T, NP>(sU[c], a.u, c, ex, ey, ez, t, valid, a, false);
     __syncthreads();
     const int xb = t * P, yb = (t / NP) * S2 + t % NP, zb = (t / NP) * P + t % NP;
-    T* out = reinterpret_cast<T*>(a.lvec) + (size_t)e * 3 * (NP * NP * NP) + (t / NP) * NP + t % NP;
+    auto* out = reinterpret_cast<typename OutT<T>::type*>(a.lvec) + (size_t)e * 3 * (NP * NP * NP) + (t / NP) * NP + t % NP;
 #pragma unroll 1
     for (int c = 0; c < 3; ++c) {
         T r[NP];
@@ -217,7 +228,7 @@ __global__ void rhs3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
         rhs_pass<T, NP, S2>(M, sU[c], sU[2], rU[2], zb, r);
         if (valid) {
 #pragma unroll
-            for (int m = 0; m < NP; ++m) out[(size_t)c * NP * NP * NP + m * NP * NP] = r[m] + (sF[zb + m * S2] + sA[zb + m * S2]);
+            for (int m = 0; m < NP; ++m) out[(size_t)c * NP * NP * NP + m * NP * NP] = to_out(r[m] + (sF[zb + m * S2] + sA[zb + m * S2]));
         }
         __syncthreads();
     }
@@ -245,7 +256,7 @@ __global__ void jac3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
     }
     __syncthreads();
     const int xb = t * P, yb = (t / NP) * S2 + t % NP, zb = (t / NP) * P + t % NP;
-    T* out = reinterpret_cast<T*>(a.lvec) + (size_t)e * 3 * (NP * NP * NP) + (t / NP) * NP + t % NP;
+    auto* out = reinterpret_cast<typename OutT<T>::type*>(a.lvec) + (size_t)e * 3 * (NP * NP * NP) + (t / NP) * NP + t % NP;
 #pragma unroll 1
     for (int c = 0; c < 3; ++c) {
         T r[NP];
@@ -257,7 +268,7 @@ __global__ void jac3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
         jac_pass<T, NP, S2>(M, sU[c], sW[c], sU[2], sW[2], rU[2], rW[2], zb, r);
         if (valid) {
 #pragma unroll
-            for (int m = 0; m < NP; ++m) out[(size_t)c * NP * NP * NP + m * NP * NP] = r[m] + (sF[zb + m * S2] + sA[zb + m * S2]);
+            for (int m = 0; m < NP; ++m) out[(size_t)c * NP * NP * NP + m * NP * NP] = to_out(r[m] + (sF[zb + m * S2] + sA[zb + m * S2]));
         }
         __syncthreads();
     }
@@ -285,7 +296,7 @@ __global__ void jact3_kernel(const __grid_constant__ OpMats<T, NP> M, const Elem
     }
     __syncthreads();
     const int xb = t * P, yb = (t / NP) * S2 + t % NP, zb = (t / NP) * P + t % NP;
-    T* out = reinterpret_cast<T*>(a.lvec) + (size_t)e * 3 * (NP * NP * NP) + (t / NP) * NP + t % NP;
+    auto* out = reinterpret_cast<typename OutT<T>::type*>(a.lvec) + (size_t)e * 3 * (NP * NP * NP) + (t / NP) * NP + t % NP;
 #pragma unroll 1
     for (int l = 0; l < 3; ++l) {
         T r[NP];
@@ -297,7 +308,7 @@ __global__ void jact3_kernel(const __grid_constant__ OpMats<T, NP> M, const Elem
         jact_pass<T, NP, S2, 3>(M, sU, sZ, rU, l, 2, zb, r);
         if (valid) {
 #pragma unroll
-            for (int m = 0; m < NP; ++m) out[(size_t)l * NP * NP * NP + m * NP * NP] = r[m] + (sF[zb + m * S2] + sA[zb + m * S2]);
+            for (int m = 0; m < NP; ++m) out[(size_t)l * NP * NP * NP + m * NP * NP] = to_out(r[m] + (sF[zb + m * S2] + sA[zb + m * S2]));
         }
         __syncthreads();
     }
@@ -322,7 +333,7 @@ __device__ __forceinline__ void rhs2_body(const OpMats<T, NP>& M, const ElemArgs
     for (int c = 0; c < 2; ++c) rU[c] = load2<T, NP>(sU[c], a.u, c, ex, ey, t, valid, a, false);
     __syncthreads();
     const int xb = t * P, yb = t;
-    T* out = reinterpret_cast<T*>(a.lvec) + (size_t)e * 2 * (NP * NP) + t;
+    auto* out = reinterpret_cast<typename OutT<T>::type*>(a.lvec) + (size_t)e * 2 * (NP * NP) + t;
 #pragma unroll 1
     for (int c = 0; c < 2; ++c) {
         T r[NP];
@@ -332,7 +343,7 @@ __device__ __forceinline__ void rhs2_body(const OpMats<T, NP>& M, const ElemArgs
         rhs_pass<T, NP, P>(M, sU[c], sU[1], rU[1], yb, r);
         if (valid) {
 #pragma unroll
-            for (int m = 0; m < NP; ++m) out[(size_t)c * NP * NP + m * NP] = r[m] + sF[yb + m * P];
+            for (int m = 0; m < NP; ++m) out[(size_t)c * NP * NP + m * NP] = to_out(r[m] + sF[yb + m * P]);
         }
         __syncthreads();
     }
@@ -365,7 +376,7 @@ __device__ __forceinline__ void jac2_body(const OpMats<T, NP>& M, const ElemArgs
     }
     __syncthreads();
     const int xb = t * P, yb = t;
-    T* out = reinterpret_cast<T*>(a.lvec) + (size_t)e * 2 * (NP * NP) + t;
+    auto* out = reinterpret_cast<typename OutT<T>::type*>(a.lvec) + (size_t)e * 2 * (NP * NP) + t;
 #pragma unroll 1
     for (int c = 0; c < 2; ++c) {
         T r[NP];
@@ -375,7 +386,7 @@ __device__ __forceinline__ void jac2_body(const OpMats<T, NP>& M, const ElemArgs
         jac_pass<T, NP, P>(M, sU[c], sW[c], sU[1], sW[1], rU[1], rW[1], yb, r);
         if (valid) {
 #pragma unroll
-            for (int m = 0; m < NP; ++m) out[(size_t)c * NP * NP + m * NP] = r[m] + sF[yb + m * P];
+            for (int m = 0; m < NP; ++m) out[(size_t)c * NP * NP + m * NP] = to_out(r[m] + sF[yb + m * P]);
         }
         __syncthreads();
     }
@@ -408,7 +419,7 @@ __device__ __forceinline__ void jact2_body(const OpMats<T, NP>& M, const ElemArg
     }
     __syncthreads();
     const int xb = t * P, yb = t;
-    T* out = reinterpret_cast<T*>(a.lvec) + (size_t)e * 2 * (NP * NP) + t;
+    auto* out = reinterpret_cast<typename OutT<T>::type*>(a.lvec) + (size_t)e * 2 * (NP * NP) + t;
 #pragma unroll 1
     for (int l = 0; l < 2; ++l) {
         T r[NP];
@@ -418,7 +429,7 @@ __device__ __forceinline__ void jact2_body(const OpMats<T, NP>& M, const ElemArg
         jact_pass<T, NP, P, 2>(M, sU, sZ, rU, l, 1, yb, r);
         if (valid) {
 #pragma unroll
-            for (int m = 0; m < NP; ++m) out[(size_t)l * NP * NP + m * NP] = r[m] + sF[yb + m * P];
+            for (int m = 0; m < NP; ++m) out[(size_t)l * NP * NP + m * NP] = to_out(r[m] + sF[yb + m * P]);
         }
         __syncthreads();
     }
@@ -479,9 +490,9 @@ __global__ void op1_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemAr
 #pragma unroll
         for (int m = 0; m < NP; ++m) f[m] = fma(-z[m], gu[m], f[m] + dv[m]);
     }
-    T* o = reinterpret_cast<T*>(a.lvec) + (size_t)e * NP;
+    auto* o = reinterpret_cast<typename OutT<T>::type*>(a.lvec) + (size_t)e * NP;
 #pragma unroll
-    for (int m = 0; m < NP; ++m) o[m] = f[m];
+    for (int m = 0; m < NP; ++m) o[m] = to_out(f[m]);
 }
 
 }  // namespace semk

@@ -33,6 +33,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "df64.cuh"
 
 namespace semk {
@@ -143,6 +145,34 @@ template <typename T, int NP, int STRIDE>
 __device__ __forceinline__ void st_line(T* s, int base, const T (&x)[NP]) {
 #pragma unroll
     for (int m = 0; m < NP; ++m) s[base + m * STRIDE] = x[m];
+}
+
+// Element-local output type: the compute type, except double for double-float
+// kernels (whose results go to the FP64 assembly).
+template <typename T>
+struct OutT {
+    using type = T;
+};
+template <>
+struct OutT<dfloat> {
+    using type = double;
+};
+
+template <typename T>
+__device__ __forceinline__ T to_out(T x) {
+    return x;
+}
+// exact: h and l widen exactly and their sum has at most 48 significant bits
+__device__ __forceinline__ double to_out(dfloat x) { return widen_bits(x.h) + widen_bits(x.l); }
+
+// Matrix coefficient in the compute type (host).
+template <typename T>
+T to_coeff(double x) {
+    return (T)x;
+}
+template <>
+inline dfloat to_coeff<dfloat>(double x) {
+    return dfloat_of(x);
 }
 
 // Launch-time arguments shared by the element kernels.

@@ -5,6 +5,7 @@
 #include <algorithm>
 
 #include "op_elem.cuh"
+#include "op_elem_lean.cuh"
 #include "sem_internal.h"
 
 namespace semk {
@@ -16,12 +17,12 @@ void split_eo(EOMat<T, NP>& M, const double* A) {
     constexpr int H = NP / 2;
     for (int i = 0; i < H; ++i) {
         for (int j = 0; j < H; ++j) {
-            M.e[i][j] = (T)(0.5 * (A[i * NP + j] + A[i * NP + (NP - 1 - j)]));
-            M.o[i][j] = (T)(0.5 * (A[i * NP + j] - A[i * NP + (NP - 1 - j)]));
+            M.e[i][j] = to_coeff<T>(0.5 * (A[i * NP + j] + A[i * NP + (NP - 1 - j)]));
+            M.o[i][j] = to_coeff<T>(0.5 * (A[i * NP + j] - A[i * NP + (NP - 1 - j)]));
         }
-        if (NP & 1) M.e[i][H] = (T)A[i * NP + H];
+        if (NP & 1) M.e[i][H] = to_coeff<T>(A[i * NP + H]);
     }
-    for (int j = 0; j <= H; ++j) M.m[j] = (NP & 1) ? (T)A[H * NP + j] : (T)0;
+    for (int j = 0; j <= H; ++j) M.m[j] = to_coeff<T>((NP & 1) ? A[H * NP + j] : 0.0);
 }
 
 constexpr int SMEM_TARGET = 100 * 1024;   // two blocks per SM fit in 227 KB
@@ -31,6 +32,7 @@ template <typename T, int D, int NP>
 size_t elem_smem_bytes(int op) {
     using Tl = Tile<NP>;
     const size_t tile = D == 3 ? Tl::S3 : (D == 2 ? Tl::S2 : 0);
+    if (D == 3 && lean3<T, NP>()) return (size_t)lean_tiles_per_elem<D>(op) * tile * sizeof(T);
     return (size_t)tiles_per_elem<D>(op) * tile * sizeof(T);
 }
 
@@ -49,8 +51,9 @@ cudaError_t launch_elem_np(int op, const double* mats, const ElemArgs& a, cudaSt
         return cudaGetLastError();
     } else {
         constexpr int TPE = D == 3 ? NP * NP : NP;
+        constexpr bool lean = D == 3 && lean3<T, NP>();
         const size_t per = elem_smem_bytes<T, D, NP>(op);
-        const int epb_max = std::max(1, std::min(256 / TPE, (int)(SMEM_TARGET / per)));
+        const int epb_max = lean ? 1 : std::max(1, std::min(256 / TPE, (int)(SMEM_TARGET / per)));
         // Balance the grid over the SMs: the fewest waves k of NUM_SMS blocks that
         // fit epb_max elements per block, then the smallest block that fills them.
         const int waves = (a.nelem + NUM_SMS * epb_max - 1) / (NUM_SMS * epb_max);
@@ -61,7 +64,10 @@ cudaError_t launch_elem_np(int op, const double* mats, const ElemArgs& a, cudaSt
         const int threads = epb * TPE;
         const int blocks = (a.nelem + epb - 1) / epb;
         void (*k)(const OpMats<T, NP>, const ElemArgs);
-        if constexpr (D == 3)
+        if constexpr (lean)
+            k = op == OP_RHS ? rhs3_lean_kernel<T, NP>
+                             : (op == OP_JAC ? jac3_lean_kernel<T, NP> : jact3_lean_kernel<T, NP>);
+        else if constexpr (D == 3)
             k = op == OP_RHS ? rhs3_kernel<T, NP> : (op == OP_JAC ? jac3_kernel<T, NP> : jact3_kernel<T, NP>);
         else
             k = op == OP_RHS ? rhs2_kernel<T, NP> : (op == OP_JAC ? jac2_kernel<T, NP> : jact2_kernel<T, NP>);

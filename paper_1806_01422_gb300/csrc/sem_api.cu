@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -89,8 +90,18 @@ bool tableau_of(int scheme, Tableau& t) {
         t.b[0] = 1.0;
         return true;
     }
+    if (scheme == SEM_BS3) {   // third-order member of the Bogacki-Shampine 3(2) pair
+        t.s = 3;
+        t.A[1][0] = 0.5;
+        t.A[2][1] = 0.75;
+        t.b[0] = 2.0 / 9.0; t.b[1] = 1.0 / 3.0; t.b[2] = 4.0 / 9.0;
+        return true;
+    }
     return false;
 }
+
+// Second-order companion weights of the pair on (k1, k2, k3, k4 = F(u_{n+1})).
+constexpr double BS3_BHAT[4] = {7.0 / 24.0, 1.0 / 4.0, 1.0 / 3.0, 1.0 / 8.0};
 
 }  // namespace
 
@@ -139,6 +150,11 @@ struct sem_ctx {
     int f_scheme = 0, f_nsteps = 0, f_mode = 0, f_slots = 0;
     double f_dt = 0;
     std::vector<int> f_ckpt;
+    // adaptive stepping (SEM_BS3 with tolerances): settings, accepted steps of the last sweep
+    double adapt_atol = 0.0, adapt_rtol = 0.0;
+    std::vector<double> f_dts;
+    long long f_rejected = 0;
+    double* adapt_buf = nullptr;
     // two-level trajectory store: states [0, f_ndev) in HBM, [f_ndev, nsteps) in pinned host memory
     size_t host_budget = 0;
     double* host_traj = nullptr;
@@ -190,6 +206,8 @@ namespace {
 constexpr int MODE_LINEAR = 100;
 // staging ring (device state slots) between the compute stream and host memory
 constexpr int TWO_LEVEL_RING = 3;
+// internal storage mode of an adaptive sweep: every accepted state, step sizes on the host
+constexpr int MODE_ADAPTIVE = 101;
 
 enum { V_K0 = 0, V_STAGE0 = 4, V_CUR0 = 7, V_CUR1 = 8, V_NU = 9, V_UN = 10, V_LAM = 11, NVEC = 12 };
 
@@ -221,7 +239,7 @@ int validate(const sem_opts* o) {
     if (o->N < 1 || o->N > 15) return fail(SEM_ERR_ARG, "N must be in [1, 15] (got %d)", o->N);
     if (!(o->nu >= 0.0) || !std::isfinite(o->nu)) return fail(SEM_ERR_ARG, "nu must be finite and >= 0");
     if (!std::isfinite(o->L)) return fail(SEM_ERR_ARG, "L must be finite");
-    if (o->precision != SEM_PREC_FP64 && o->precision != SEM_PREC_FP32_BULK)
+    if (o->precision != SEM_PREC_FP64 && o->precision != SEM_PREC_FP32_BULK && o->precision != SEM_PREC_FP64_DF)
         return fail(SEM_ERR_ARG, "unknown precision %d", o->precision);
     if (o->ckpt_mode < SEM_CKPT_AUTO || o->ckpt_mode > SEM_CKPT_TWO_LEVEL)
         return fail(SEM_ERR_ARG, "unknown checkpoint mode %d", o->ckpt_mode);
@@ -355,9 +373,18 @@ int apply(sem_t h, int op, const double* u, const double* w, const Epi& ep, cuda
     long long slot;
     SEM_TRY(prof_begin(h, op, s, slot));
     cudaError_t e;
-    if (h->dim == 1) e = f32 ? launch_elem<float, 1>(h->np, op, h->mats.data(), a, s) : launch_elem<double, 1>(h->np, op, h->mats.data(), a, s);
-    else if (h->dim == 2) e = f32 ? launch_elem<float, 2>(h->np, op, h->mats.data(), a, s) : launch_elem<double, 2>(h->np, op, h->mats.data(), a, s);
-    else e = f32 ? launch_elem<float, 3>(h->np, op, h->mats.data(), a, s) : launch_elem<double, 3>(h->np, op, h->mats.data(), a, s);
+    const double* mt = h->mats.data();
+    if (h->precision == SEM_PREC_FP64_DF) {   // double-float element arithmetic, FP64 everywhere else
+        if (h->dim == 1) e = launch_elem<dfloat, 1>(h->np, op, mt, a, s);
+        else if (h->dim == 2) e = launch_elem<dfloat, 2>(h->np, op, mt, a, s);
+        else e = launch_elem<dfloat, 3>(h->np, op, mt, a, s);
+    } else if (h->dim == 1) {
+        e = f32 ? launch_elem<float, 1>(h->np, op, mt, a, s) : launch_elem<double, 1>(h->np, op, mt, a, s);
+    } else if (h->dim == 2) {
+        e = f32 ? launch_elem<float, 2>(h->np, op, mt, a, s) : launch_elem<double, 2>(h->np, op, mt, a, s);
+    } else {
+        e = f32 ? launch_elem<float, 3>(h->np, op, mt, a, s) : launch_elem<double, 3>(h->np, op, mt, a, s);
+    }
     if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "element kernel launch: %s", cudaGetErrorString(e));
     SEM_TRY(prof_end(h, slot, s));
     AsmArgs aa;
@@ -481,7 +508,8 @@ int rk_stages(sem_t h, const Tableau& T, double dt, const double* un, double* co
 // On entry vec(V_NU) holds nu_{s-1} = dt b_{s-1} lam; on exit it holds the same
 // quantity for the updated lam (the next step's first stage).  lam is updated in place.
 int rk_adjoint_step(sem_t h, const Tableau& T, double dt, const double* const* Y, double* lam,
-                    cudaStream_t s, long long& count) {
+                    cudaStream_t s, long long& count, double dt_next = -1.0) {
+    if (dt_next < 0) dt_next = dt;   // step size of the next (earlier) step, for its nu_{s-1}
     double* nu = vec(h, V_NU);
     if (subdiagonal(T) && T.s > 1) {
         // nu_{i-1} = dt (b_{i-1} lam + a_{i,i-1} mu_i) and the running sum
@@ -508,7 +536,7 @@ int rk_adjoint_step(sem_t h, const Tableau& T, double dt, const double* const* Y
                 ep.out[0] = lam;
                 ep.alpha[0] = 1.0;
                 ep.beta[0][sa] = 1.0;
-                const double c = dt * T.b[T.s - 1];
+                const double c = dt_next * T.b[T.s - 1];
                 ep.out[1] = nu;
                 ep.alpha[1] = c;
                 ep.beta[1][sa] = c;
@@ -539,7 +567,7 @@ int rk_adjoint_step(sem_t h, const Tableau& T, double dt, const double* const* Y
             ep.alpha[0] = 1.0;
             ep.beta[0][sl] = 1.0;
             for (int j = 1; j < T.s; ++j) ep.beta[0][add_src(ep, vec(h, V_K0 + j))] = 1.0;
-            const double c = dt * T.b[T.s - 1];
+            const double c = dt_next * T.b[T.s - 1];
             ep.out[1] = nu;
             ep.alpha[1] = c;
             for (int m = 0; m < ep.nsrc; ++m) ep.beta[1][m] = c * ep.beta[0][m];
@@ -652,6 +680,8 @@ int check_flag(sem_t h, cudaStream_t s, const char* what) {
 
 int cn_forward(sem_t h, double dt, int nsteps, const double* u0, double* uT, cudaStream_t s);
 int cn_adjoint(sem_t h, const double* lamT, double* lam0, cudaStream_t s);
+int adaptive_forward(sem_t h, double T, double dt0, const double* u0, double* uT, cudaStream_t s);
+bool adaptive(sem_t h, int scheme) { return scheme == SEM_BS3 && (h->adapt_atol > 0.0 || h->adapt_rtol > 0.0); }
 
 // uT_internal: uT is a handle work state (float pairs in the FP32 form) rather
 // than the caller's double output.
@@ -666,6 +696,7 @@ int forward_impl(sem_t h, int scheme, double dt, int nsteps, const double* u0, d
     if (overlap(u0, uT, vec_bytes(h))) return fail(SEM_ERR_ALIAS, "uT overlaps u0");
     SEM_TRY(ensure_workspace(h));
     if (scheme == SEM_CN) return cn_forward(h, dt, nsteps, u0, uT, s);
+    if (adaptive(h, scheme)) return adaptive_forward(h, dt * nsteps, dt, u0, uT, s);
     int mode, slots;
     SEM_TRY(choose_mode(h, T.s, nsteps, mode, slots));
     if (mode == SEM_CKPT_BINOMIAL && slots > nsteps) slots = nsteps;
@@ -818,7 +849,16 @@ int adjoint_impl(sem_t h, const double* lamT, double* lam0, cudaStream_t s, bool
     }
     long long nrhs = 0, njt = 0;
     double* Yw[4] = {nullptr, vec(h, V_STAGE0), vec(h, V_STAGE0 + 1), vec(h, V_STAGE0 + 2)};
-    if (h->f_mode == MODE_LINEAR) {
+    if (h->f_mode == MODE_ADAPTIVE) {
+        // accepted steps in reverse, each with its own step size; stages recomputed from its state
+        for (int n = nsteps - 1; n >= 0; --n) {
+            double* un = h->traj + (size_t)n * h->ndof;
+            Yw[0] = un;
+            SEM_TRY(rk_stages(h, T, h->f_dts[n], un, Yw, nullptr, s, nrhs));
+            const double* Y[4] = {Yw[0], Yw[1], Yw[2], Yw[3]};
+            SEM_TRY(rk_adjoint_step(h, T, h->f_dts[n], Y, lam0, s, njt, n > 0 ? h->f_dts[n - 1] : h->f_dts[n]));
+        }
+    } else if (h->f_mode == MODE_LINEAR) {
         if (!h->frozen) return fail(SEM_ERR_STATE, "the advecting field changed after the forward sweep");
         const double* Y[4] = {h->frozen, h->frozen, h->frozen, h->frozen};
         for (int n = nsteps - 1; n >= 0; --n) SEM_TRY(rk_adjoint_step(h, T, dt, Y, lam0, s, njt));
@@ -1193,6 +1233,156 @@ int cn_adjoint(sem_t h, const double* lamT, double* lam0, cudaStream_t s) {
     return SEM_OK;
 }
 
+// ------------------------------------------------------------------ adaptive stepping
+// Sec. 5.1: the step is chosen from a weighted estimate of the local truncation
+// error.  Pair: Bogacki-Shampine 3(2); error E = dt sum_i (b_i - bhat_i) k_i with
+// k4 = F(u_{n+1}), in the weighted RMS norm with atol + rtol max(|u_n|, |u_{n+1}|);
+// controller: accept when err <= 1, next trial dt min(fmax, max(0.2, 0.9 err^(-1/3)))
+// with fmax = 5 (1 right after a rejection); the last step ends on the horizon.
+// The stage epilogues carry the solution and the error estimate as running sums.
+// One device-to-host read of the error norm per attempted step decides it.
+
+// Keep the first `keep` trajectory vectors while growing the buffer to hold nvec.
+int grow_traj(sem_t h, size_t nvec, size_t keep, cudaStream_t s) {
+    if (h->traj && h->traj_vectors >= nvec) return SEM_OK;
+    const size_t vb = vec_bytes(h);
+    size_t cap = std::max<size_t>(std::max<size_t>(nvec, 2 * h->traj_vectors), 16);
+    if (h->ckpt_budget) cap = std::min(cap, h->ckpt_budget / vb);
+    if (cap < nvec) return fail(SEM_ERR_OOM, "adaptive sweep: %zu states exceed the budget of %zu bytes", nvec,
+                                h->ckpt_budget);
+    double* nb = nullptr;
+    cudaError_t e = cudaMalloc((void**)&nb, cap * vb);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? SEM_ERR_OOM : SEM_ERR_CUDA,
+                    "adaptive sweep: trajectory of %zu bytes: %s", cap * vb, cudaGetErrorString(e));
+    }
+    if (h->traj && keep) SEM_CK(cudaMemcpyAsync(nb, h->traj, keep * vb, cudaMemcpyDeviceToDevice, s));
+    SEM_CK(cudaStreamSynchronize(s));
+    cudaFree(h->traj);
+    h->traj = nb;
+    h->traj_vectors = cap;
+    return SEM_OK;
+}
+
+// One attempted step u -> unext with its error estimate in err (FP64 form).
+int bs3_attempt(sem_t h, double dt, const double* u, double* unext, double* err, cudaStream_t s) {
+    Tableau T;
+    tableau_of(SEM_BS3, T);
+    double* Y1 = vec(h, V_STAGE0);
+    double* Y2 = vec(h, V_STAGE0 + 1);
+    double* acc = vec(h, V_K0);
+    for (int i = 0; i < 4; ++i) {
+        Epi ep;
+        std::memset(&ep, 0, sizeof(ep));
+        ep.nonfinite = h->flag;
+        const double d = dt * ((i < 3 ? T.b[i] : 0.0) - BS3_BHAT[i]);
+        const double* at = i == 0 ? u : (i == 1 ? Y1 : (i == 2 ? Y2 : unext));
+        if (i < 2) {   // next stage, running solution, running error
+            const int su = add_src(ep, u);
+            ep.out[0] = i == 0 ? Y1 : Y2;
+            ep.alpha[0] = dt * T.A[i + 1][i];
+            ep.beta[0][su] = 1.0;
+            const int sa = i == 0 ? su : add_src(ep, acc);
+            ep.out[1] = acc;
+            ep.alpha[1] = dt * T.b[i];
+            ep.beta[1][sa] = 1.0;
+            ep.out[2] = err;
+            ep.alpha[2] = d;
+            if (i > 0) ep.beta[2][add_src(ep, err)] = 1.0;
+            ep.nout = 3;
+        } else if (i == 2) {   // the solution, running error
+            const int sa = add_src(ep, acc);
+            ep.out[0] = unext;
+            ep.alpha[0] = dt * T.b[2];
+            ep.beta[0][sa] = 1.0;
+            ep.out[1] = err;
+            ep.alpha[1] = d;
+            ep.beta[1][add_src(ep, err)] = 1.0;
+            ep.nout = 2;
+        } else {   // k4 = F(u_{n+1}) enters the error only
+            ep.out[0] = err;
+            ep.alpha[0] = d;
+            ep.beta[0][add_src(ep, err)] = 1.0;
+            ep.nout = 1;
+        }
+        SEM_TRY(stage_rhs(h, at, ep, s));
+    }
+    return SEM_OK;
+}
+
+int adaptive_forward(sem_t h, double T, double dt0, const double* u0, double* uT, cudaStream_t s) {
+    if (f32(h)) return fail(SEM_ERR_ARG, "adaptive stepping runs in the FP64 form only");
+    const size_t vb = vec_bytes(h);
+    h->have_fwd = false;
+    SEM_TRY(grow_traj(h, 2, 0, s));
+    SEM_CK(cudaMemcpyAsync(h->traj, u0, vb, cudaMemcpyDeviceToDevice, s));
+    std::vector<double> dts;
+    long long rejected = 0, count = 0;
+    double t = 0.0, dt = dt0;
+    bool after_reject = false;
+    double* err = vec(h, V_K0 + 1);
+    if (!h->adapt_buf) {   // partial sums of the error norm and its total
+        cudaError_t e = cudaMalloc((void**)&h->adapt_buf, sizeof(double) * (multidot_blocks(h->ndof) + 1));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->adapt_buf = nullptr;
+            return fail(SEM_ERR_OOM, "adaptive sweep workspace: %s", cudaGetErrorString(e));
+        }
+    }
+    double* part = h->adapt_buf + 1;
+    double* total = h->adapt_buf;
+    while (t < T) {
+        if (dts.size() >= 10000000) return fail(SEM_ERR_NONFINITE, "adaptive sweep: more than 1e7 steps");
+        const bool last = t + dt >= T * (1.0 - 1e-12);
+        const double step = last ? T - t : dt;
+        const size_t n = dts.size();
+        SEM_TRY(grow_traj(h, n + 2, n + 1, s));
+        double* un = h->traj + n * h->ndof;
+        double* next = h->traj + (n + 1) * h->ndof;
+        SEM_TRY(bs3_attempt(h, step, un, next, err, s));
+        count += 4;
+        cudaError_t e = launch_wrms_sum(err, un, next, h->adapt_atol, h->adapt_rtol, h->ndof, part, total, s);
+        if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "error norm launch: %s", cudaGetErrorString(e));
+        double sum = 0.0;
+        unsigned flag = 0;
+        SEM_CK(cudaMemcpyAsync(&sum, total, sizeof(double), cudaMemcpyDeviceToHost, s));
+        SEM_CK(cudaMemcpyAsync(&flag, h->flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        SEM_CK(cudaStreamSynchronize(s));
+        double enorm = std::sqrt(sum / (double)h->ndof);
+        if (flag) {   // a non-finite attempt is rejected like a too-large error
+            SEM_CK(cudaMemsetAsync(h->flag, 0, sizeof(unsigned), s));
+            enorm = std::numeric_limits<double>::infinity();
+        }
+        const double fmax = after_reject ? 1.0 : 5.0;
+        const double fac = enorm > 0.0 ? std::min(fmax, std::max(0.2, 0.9 * std::pow(enorm, -1.0 / 3.0))) : fmax;
+        if (enorm <= 1.0) {
+            dts.push_back(step);
+            t = last ? T : t + step;
+            if (!last) dt = step * fac;
+            after_reject = false;
+        } else {
+            ++rejected;
+            after_reject = true;
+            dt = step * fac;
+            if (!(dt > 1e-14 * T)) return fail(SEM_ERR_NONFINITE, "adaptive sweep: step size underflow at t = %g", t);
+        }
+    }
+    const int N = (int)dts.size();
+    SEM_CK(cudaMemcpyAsync(uT, h->traj + (size_t)N * h->ndof, vb, cudaMemcpyDeviceToDevice, s));
+    h->have_fwd = true;
+    h->f_scheme = SEM_BS3;
+    h->f_nsteps = N;
+    h->f_dt = dts.back();
+    h->f_mode = MODE_ADAPTIVE;
+    h->f_slots = 0;
+    h->f_ckpt.clear();
+    h->f_dts = dts;
+    h->f_rejected = rejected;
+    h->st[0] = count;
+    return SEM_OK;
+}
+
 // ------------------------------------------------------------------ batches
 template <typename T>
 int upload(T** dst, const std::vector<T>& src) {
@@ -1390,6 +1580,7 @@ void sem_destroy(sem_t h) {
     cudaFree(h->kpart);
     cudaFree(h->kscal);
     cudaFree(h->frozen);
+    cudaFree(h->adapt_buf);
     if (h->host_traj) cudaFreeHost(h->host_traj);
     for (int k = 0; k < 3; ++k) {
         if (h->ev_comp[k]) cudaEventDestroy(h->ev_comp[k]);
@@ -1575,7 +1766,7 @@ int sem_objective_grad(sem_t h, int scheme, double dt, int nsteps, const double*
     cudaStream_t s = (cudaStream_t)stream;
     // the implicit scheme synchronises with the host inside its solves, and the two-level
     // store runs a second stream: neither is captured
-    bool graph = h->graph_on && scheme != SEM_CN;
+    bool graph = h->graph_on && scheme != SEM_CN && !adaptive(h, scheme);
     if (graph) {
         Tableau T;
         int mode, slots;
@@ -1661,6 +1852,25 @@ int sem_set_advection(sem_t h, const double* a, void* stream) {
     return SEM_OK;
 }
 
+int sem_set_adaptive(sem_t h, double atol, double rtol) {
+    if (!h) return fail(SEM_ERR_ARG, "null handle");
+    if (!(atol >= 0.0) || !(rtol >= 0.0) || !std::isfinite(atol) || !std::isfinite(rtol))
+        return fail(SEM_ERR_ARG, "tolerances must be finite and >= 0");
+    if (f32(h) && (atol > 0.0 || rtol > 0.0)) return fail(SEM_ERR_ARG, "adaptive stepping runs in the FP64 form only");
+    h->adapt_atol = atol;
+    h->adapt_rtol = rtol;
+    return SEM_OK;
+}
+
+int sem_adaptive_steps(sem_t h, int* accepted, int* rejected, double* dts, int cap) {
+    if (!h || !accepted || !rejected || cap < 0 || (cap > 0 && !dts)) return fail(SEM_ERR_ARG, "bad arguments");
+    const bool ok = h->have_fwd && h->f_mode == MODE_ADAPTIVE;
+    *accepted = ok ? (int)h->f_dts.size() : 0;
+    *rejected = ok ? (int)h->f_rejected : 0;
+    for (int i = 0; ok && i < cap && i < *accepted; ++i) dts[i] = h->f_dts[i];
+    return SEM_OK;
+}
+
 int sem_set_host_tier(sem_t h, size_t host_bytes) {
     if (!h) return fail(SEM_ERR_ARG, "null handle");
     if (h->host_traj && host_bytes < h->host_vectors * vec_bytes(h)) {
@@ -1679,6 +1889,11 @@ int sem_trajectory_info(sem_t h, long long* out4) {
     if (!h || !out4) return fail(SEM_ERR_ARG, "null handle or output");
     out4[0] = out4[1] = out4[2] = out4[3] = 0;
     if (!h->have_fwd || h->f_mode == MODE_LINEAR) return SEM_OK;
+    if (h->f_mode == MODE_ADAPTIVE) {
+        out4[0] = SEM_CKPT_STATES;
+        out4[1] = h->f_nsteps + 1;
+        return SEM_OK;
+    }
     Tableau T;
     const int stages = h->f_scheme == SEM_CN ? 1 : (tableau_of(h->f_scheme, T) ? T.s : 1);
     out4[0] = h->f_mode;
@@ -1872,7 +2087,7 @@ const char* sem_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"
 
-int semk::max_np(int D, bool fp32) { return (D == 3 && !fp32) ? 12 : 16; }
+int semk::max_np(int D, bool fp32) { return (void)D, (void)fp32, 16; }
 
 // Read-only view of a handle for entry points defined in other translation units.
 int semk::handle_view(sem_t h, HandleView* v) {

@@ -128,6 +128,10 @@ struct VecList { const double* v[KMAX]; };
 int multidot_blocks(size_t n);
 cudaError_t launch_multidot(const VecList& V, int k, const double* w, size_t n, double* partials, double* out,
                             cudaStream_t s);
+// out[0] = sum_i (e_i / (atol + rtol max(|u0_i|, |u1_i|)))^2 (fixed-order block reduction;
+// partials: multidot_blocks(n) doubles)
+cudaError_t launch_wrms_sum(const double* e, const double* u0, const double* u1, double atol, double rtol, size_t n,
+                            double* partials, double* out, cudaStream_t s);
 cudaError_t launch_multiaxpy(double* w, const VecList& V, int k, const double* coef, double scale, size_t n,
                              cudaStream_t s);
 

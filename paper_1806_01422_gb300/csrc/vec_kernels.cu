@@ -549,6 +549,34 @@ cudaError_t launch_multidot(const VecList& V, int k, const double* w, size_t n, 
     return cudaGetLastError();
 }
 
+// partials[block] = sum over the block's range of (e_i / (atol + rtol max(|u0_i|, |u1_i|)))^2
+__global__ void __launch_bounds__(MD_THREADS) wrms_kernel(const double* __restrict__ e, const double* __restrict__ u0,
+                                                          const double* __restrict__ u1, double atol, double rtol,
+                                                          size_t n, double* __restrict__ partials) {
+    __shared__ double ws[MD_THREADS / 32];
+    double acc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)MD_THREADS + threadIdx.x; i < n; i += (size_t)gridDim.x * MD_THREADS) {
+        const double r = e[i] / (atol + rtol * fmax(fabs(u0[i]), fabs(u1[i])));
+        acc = fma(r, r, acc);
+    }
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < MD_THREADS / 32 ? ws[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) partials[blockIdx.x] = v;
+    }
+}
+
+cudaError_t launch_wrms_sum(const double* e, const double* u0, const double* u1, double atol, double rtol, size_t n,
+                            double* partials, double* out, cudaStream_t s) {
+    const int nb = multidot_blocks(n);
+    wrms_kernel<<<nb, MD_THREADS, 0, s>>>(e, u0, u1, atol, rtol, n, partials);
+    multidot_final<<<1, 256, 0, s>>>(partials, nb, out);
+    return cudaGetLastError();
+}
+
 // w += sum_j (+-coef[j]) V_j; the sign is an operand modifier of the FMA (no extra FP64 multiply)
 template <bool NEG>
 __global__ void multiaxpy_kernel(double* __restrict__ w, const VecList V, int k, const double* __restrict__ coef,

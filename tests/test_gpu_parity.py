@@ -43,7 +43,8 @@ def smooth(g, seed):
 
 
 OPS = [(1, 3, 3), (1, 16, 7), (1, 1, 4), (1, 5, 15), (2, 1, 3), (2, 2, 2), (2, 3, 4), (2, 5, 7),
-       (2, 3, 15), (3, 1, 4), (3, 2, 2), (3, 3, 3), (3, 3, 7), (3, 2, 11)]
+       (2, 3, 15), (3, 1, 4), (3, 2, 2), (3, 3, 3), (3, 3, 7), (3, 2, 11), (3, 2, 12), (3, 1, 15), (3, 2, 13),
+       (3, 2, 15)]
 
 
 @pytest.mark.parametrize("dim,E,N", OPS)
