@@ -75,14 +75,19 @@ PEAK_DF_TFLOPS = 152 * 128 * 2.07e9 / 13 * 2 / 1e12
 # valid only while the kernel sources hash to the recorded value.
 TRAFFIC = {
     "jact2_kernel<double,8>@2d@fp64": {
-        "bytes": 6477312 + 0, "src": "e1753eeccab48628",
+        "bytes": 6477568 + 0, "src": "4614f8cb473058eb",
         "capture": "dram__bytes_read.sum + dram__bytes_write.sum of one jact2 launch at 64x64 quads, N=7 "
                    "(ncu --set full; profiles/rhs2_jact2_assemble_2d_fp64_E64_N7.md)"},
+    "jact2_kernel<semk::dfa::dfloat,8>@2d@fp64_df": {
+        "bytes": 6573056 + 0, "src": "4614f8cb473058eb",
+        "capture": "dram__bytes_read.sum + dram__bytes_write.sum of one J^T launch (op2c_kernel) at 64x64 "
+                   "quads, N=7 (ncu --set full; profiles/rhs2_jact2_2d_fp64df_E64_N7.md)"},
 }
 
 # sources of the element kernels (rhs*, jac*, jact*) and of the assembly kernels
-KERNEL_SOURCES = {"elem": ["op_kernels.cuh", "op_elem.cuh", "op_launch.cuh", "df64.cuh", "op_d1.cu", "op_d2.cu",
-                           "op_d3.cu"],
+KERNEL_SOURCES = {"elem": ["op_kernels.cuh", "op_elem.cuh", "op_elem_lean.cuh", "op_launch.cuh", "df64.cuh",
+                           "op_d1.cu", "op_d2.cu", "op_d2_df.cu", "op_d3.cu", "op_d3_f.cu", "op_d3_df.cu",
+                           "op_d3_df_mid.cu", "op_d3_df_hi.cu"],
                   "assemble": ["vec_kernels.cu", "df64.cuh"]}
 
 
@@ -265,6 +270,92 @@ def reference_arm(args, world, rank):
             "e2e": {"value": value, "unit": "gradient evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def roofline_of(prof, args, w, s, precision):
+    """Roofline of the dominant kernel kind from the sampled CUDA-event times of a timed region."""
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dom_ms, dom_n = kinds[dom]
+    avg_s = dom_ms / dom_n / 1e3
+    fp32 = precision == "fp32_bulk"
+    names = {"rhs": "rhs", "jac": "jac", "jacT": "jact"}
+    if args.workload == "batch":
+        shapes = list(zip(s.E, s.N))
+        kname = "batch_elem2_kernel"
+    else:
+        shapes = [(w["E"], w["N"])]
+        kname = None
+    if dom == "assemble":
+        # gather-scatter of one plain apply: reads the d E^d (N+1)^d element-local values and
+        # writes the d (E N)^d unknowns (the RK epilogue's sources are not counted)
+        vb = 4 if fp32 else 8
+        d = w["dim"]
+        bytes_per = sum(d * (E * (N + 1)) ** d * vb + d * (E * N) ** d * 8 for E, N in shapes)
+        achieved = bytes_per / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": args.hbm_peak, "unit": "GB/s",
+                "frac": achieved / args.hbm_peak, "kernel": "assemble kernel"}
+    else:
+        flops = sum(algorithmic_flops_per_element(dom, w["dim"], N + 1) * E ** w["dim"] for E, N in shapes)
+        achieved = flops / avg_s / 1e12
+        dfk = precision == "fp64_df"
+        peak = PEAK_FP32_TFLOPS if fp32 else (PEAK_DF_TFLOPS if dfk else PEAK_FP64_TFLOPS)
+        ctype = "float" if fp32 else ("semk::dfa::dfloat" if dfk else "double")
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "kernel": kname or "%s%d_kernel<%s,%d>" % (names[dom], w["dim"], ctype, w["N"] + 1)}
+        if dfk:
+            roof["peak_note"] = ("double-float multiply-add rate of the FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz "
+                                 "/ 13 FP32 operations per multiply-add, x 2 flop")
+    key = "%s@%s@%s" % (roof["kernel"], args.workload, precision)
+    tr = TRAFFIC.get(key)
+    tr_ok = tr and tr["src"] == kernel_src_hash("assemble" if dom == "assemble" else "elem")
+    roof["traffic"] = tr["bytes"] if tr_ok else None
+    if tr_ok:
+        roof["traffic_source"] = tr["capture"]
+    if roof["bound"] == "alu":
+        roof["note"] = ("achieved counts the algorithmic flops of plain n-term contractions; the kernels split "
+                        "each contraction into even and odd halves (n^2/2 + n operations per line), so frac can "
+                        "exceed the fraction of FP pipe cycles ncu reports")
+    roof["avg_launch_us"] = avg_s * 1e6
+    roof["timed_launches"] = dom_n
+    roof["timing"] = "CUDA events around 1 in %d launches of each kernel kind, on the launching stream%s, " \
+                     "inside the timed region" % (args.profile_every,
+                                                  "" if args.no_graph else " (event nodes of the replayed graph)")
+
+    return roof
+
+
+def measure_form(args, w, precision, u0, uo, grad_ref, J_ref, dev):
+    """Gradient evaluations/s of another precision form on the same inputs (same timing rules), its
+    dominant kernel's roofline, and its misfit and gradient against the FP64 form's."""
+    import torch
+    from paper_1806_01422_gb300 import Sem
+    s = Sem(w["dim"], w["E"], w["N"], w["nu"], precision=precision, ckpt=w["ckpt"], ckpt_slots=w["slots"],
+            device=dev)
+    g = s.empty()
+    s.use_graph(not args.no_graph)
+    s.profile(args.profile_every)
+    for _ in range(max(3, args.warmup)):
+        J, _ = s.objective_grad(u0, uo, w["dt"], w["nsteps"], w["scheme"], grad=g)
+    s.profile_read(reset=True)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(args.steps):
+        J, _ = s.objective_grad(u0, uo, w["dt"], w["nsteps"], w["scheme"], grad=g)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    s.profile(0)
+    prof = s.profile_read(reset=True)
+    elapsed = e0.elapsed_time(e1) / 1e3
+    roof = roofline_of(prof, args, w, s, precision)
+    out = {"value": args.steps / elapsed, "ms_per_step": elapsed / args.steps * 1e3,
+           "J_rel_diff_vs_fp64": abs(J - J_ref) / abs(J_ref),
+           "grad_rel_err_vs_fp64": float((g - grad_ref).abs().max() / grad_ref.abs().max()),
+           "roofline": {k: roof[k] for k in ("bound", "achieved", "peak", "unit", "frac", "kernel", "avg_launch_us")}}
+    s.close()
+    return out
+
+
 def gpu_arm(args, world, rank, local):
     import torch
     from paper_1806_01422_gb300 import Sem, inputs
@@ -345,54 +436,8 @@ def gpu_arm(args, world, rank, local):
         launches = args.steps * (2 * cs["applies"] + 13 * krylov + 4 * (cs["newton"] + nsteps)
                                  + 5 * cs["newton"] + 3)
 
-    # dominant kernel of the timed region and its roofline
-    kinds = {k: v for k, v in prof.items() if v[1] > 0}
-    dom = max(kinds, key=lambda k: kinds[k][0])
-    dom_ms, dom_n = kinds[dom]
-    avg_s = dom_ms / dom_n / 1e3
+    roof = roofline_of(prof, args, w, s, args.precision)
     fp32 = args.precision == "fp32_bulk"
-    names = {"rhs": "rhs", "jac": "jac", "jacT": "jact"}
-    if args.workload == "batch":
-        shapes = list(zip(s.E, s.N))
-        kname = "batch_elem2_kernel"
-    else:
-        shapes = [(w["E"], w["N"])]
-        kname = None
-    if dom == "assemble":
-        # gather-scatter of one plain apply: reads the d E^d (N+1)^d element-local values and
-        # writes the d (E N)^d unknowns (the RK epilogue's sources are not counted)
-        vb = 4 if fp32 else 8
-        d = w["dim"]
-        bytes_per = sum(d * (E * (N + 1)) ** d * vb + d * (E * N) ** d * 8 for E, N in shapes)
-        achieved = bytes_per / avg_s / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": args.hbm_peak, "unit": "GB/s",
-                "frac": achieved / args.hbm_peak, "kernel": "assemble kernel"}
-    else:
-        flops = sum(algorithmic_flops_per_element(dom, w["dim"], N + 1) * E ** w["dim"] for E, N in shapes)
-        achieved = flops / avg_s / 1e12
-        dfk = args.precision == "fp64_df"
-        peak = PEAK_FP32_TFLOPS if fp32 else (PEAK_DF_TFLOPS if dfk else PEAK_FP64_TFLOPS)
-        ctype = "float" if fp32 else ("semk::dfa::dfloat" if dfk else "double")
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "kernel": kname or "%s%d_kernel<%s,%d>" % (names[dom], w["dim"], ctype, w["N"] + 1)}
-        if dfk:
-            roof["peak_note"] = ("double-float multiply-add rate of the FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz "
-                                 "/ 13 FP32 operations per multiply-add, x 2 flop")
-    key = "%s@%s@%s" % (roof["kernel"], args.workload, args.precision)
-    tr = TRAFFIC.get(key)
-    tr_ok = tr and tr["src"] == kernel_src_hash("assemble" if dom == "assemble" else "elem")
-    roof["traffic"] = tr["bytes"] if tr_ok else None
-    if tr_ok:
-        roof["traffic_source"] = tr["capture"]
-    if roof["bound"] == "alu":
-        roof["note"] = ("achieved counts the algorithmic flops of plain n-term contractions; the kernels split "
-                        "each contraction into even and odd halves (n^2/2 + n operations per line), so frac can "
-                        "exceed the fraction of FP pipe cycles ncu reports")
-    roof["avg_launch_us"] = avg_s * 1e6
-    roof["timed_launches"] = dom_n
-    roof["timing"] = "CUDA events around 1 in %d launches of each kernel kind, on the launching stream%s, " \
-                     "inside the timed region" % (args.profile_every,
-                                                  "" if args.no_graph else " (event nodes of the replayed graph)")
 
     unit = "instance gradient evals/s" if args.workload == "batch" else "gradient evals/s"
     stages = {"rk4": 4, "ssprk3": 3, "euler": 1, "cn": 1}[scheme]
@@ -414,6 +459,10 @@ def gpu_arm(args, world, rank, local):
     if scheme == "cn":
         out["solver"] = dict(s.solver_stats(), note="counters of the last gradient evaluation")
 
+    if rank == 0 and not args.no_extras and args.precision == "fp64" and w["scheme"] != "cn" \
+            and args.workload != "batch":
+        # the other precision forms on the same inputs, reported against this FP64 form
+        out["forms"] = {p: measure_form(args, w, p, u0, uo, grad, J, dev) for p in ("fp64_df", "fp32_bulk")}
     if rank == 0 and not args.no_extras:
         out.update(extras(s, u0, uo, w, dev))
         # end to end through the public API with host buffers (pinned), copies inside the timed region

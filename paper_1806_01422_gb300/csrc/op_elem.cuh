@@ -443,6 +443,108 @@ __global__ void jact2_kernel(const __grid_constant__ OpMats<T, NP> M, const Elem
     jact2_body<T, NP>(M, a, e, t, el, e < a.nelem, smem_raw);
 }
 
+// ================================================================== d = 2, one thread per (line, component)
+// Double-float kernels are bound by latency, not by a pipe: a 2D grid has too few
+// lines to hide the dependent chains of a compensated multiply-add.  These bodies
+// give each output component its own thread (2n threads per element): thread
+// (t, c) runs the x and y passes of component c, with one partial tile per
+// component.  The per-thread work halves and the thread count doubles; the
+// passes and the summation order are those of the bodies above.
+template <typename T, int NP>
+__device__ __forceinline__ void rhs2c_body(const OpMats<T, NP>& M, const ElemArgs& a, int e, int t, int c, int el,
+                                         bool valid, unsigned char* smem_raw) {
+    static_assert(!RefSub<T>::on, "component-parallel bodies assume no reference subtraction");
+    using Tl = Tile<NP>;
+    constexpr int P = Tl::P, S2 = Tl::S2;
+    T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)el * (tiles_per_elem<2>(OP_RHS) + 1) * S2;
+    T* sU[2] = {sm, sm + S2};
+    T* sF = sm + (2 + c) * S2;
+    const int ex = e % a.E, ey = e / a.E;
+    const T ru0 = load2<T, NP>(sU[c], a.u, c, ex, ey, t, valid, a, false);
+    (void)ru0;
+    __syncthreads();
+    const T rU[2] = {(T)0, (T)0};   // no reference subtraction in this form
+    const int xb = t * P, yb = t;
+    auto* out = reinterpret_cast<typename OutT<T>::type*>(a.lvec) + (size_t)e * 2 * (NP * NP) + (size_t)c * NP * NP + t;
+    T r[NP];
+    rhs_pass<T, NP, 1>(M, sU[c], sU[0], rU[0], xb, r);
+    st_line<T, NP, 1>(sF, xb, r);
+    __syncthreads();
+    rhs_pass<T, NP, P>(M, sU[c], sU[1], rU[1], yb, r);
+    if (valid) {
+#pragma unroll
+        for (int m = 0; m < NP; ++m) out[m * NP] = to_out(r[m] + sF[yb + m * P]);
+    }
+}
+
+template <typename T, int NP>
+__device__ __forceinline__ void jac2c_body(const OpMats<T, NP>& M, const ElemArgs& a, int e, int t, int c, int el,
+                                         bool valid, unsigned char* smem_raw) {
+    static_assert(!RefSub<T>::on, "component-parallel bodies assume no reference subtraction");
+    using Tl = Tile<NP>;
+    constexpr int P = Tl::P, S2 = Tl::S2;
+    T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)el * (tiles_per_elem<2>(OP_JAC) + 1) * S2;
+    T* sU[2] = {sm, sm + S2};
+    T* sW[2] = {sm + 2 * S2, sm + 3 * S2};
+    T* sF = sm + (4 + c) * S2;
+    const int ex = e % a.E, ey = e / a.E;
+    load2<T, NP>(sU[c], a.u, c, ex, ey, t, valid, a, false);
+    load2<T, NP>(sW[c], a.w, c, ex, ey, t, valid, a, false);
+    __syncthreads();
+    const T rz = (T)0;
+    const int xb = t * P, yb = t;
+    auto* out = reinterpret_cast<typename OutT<T>::type*>(a.lvec) + (size_t)e * 2 * (NP * NP) + (size_t)c * NP * NP + t;
+    T r[NP];
+    jac_pass<T, NP, 1>(M, sU[c], sW[c], sU[0], sW[0], rz, rz, xb, r);
+    st_line<T, NP, 1>(sF, xb, r);
+    __syncthreads();
+    jac_pass<T, NP, P>(M, sU[c], sW[c], sU[1], sW[1], rz, rz, yb, r);
+    if (valid) {
+#pragma unroll
+        for (int m = 0; m < NP; ++m) out[m * NP] = to_out(r[m] + sF[yb + m * P]);
+    }
+}
+
+template <typename T, int NP>
+__device__ __forceinline__ void jact2c_body(const OpMats<T, NP>& M, const ElemArgs& a, int e, int t, int l, int el,
+                                          bool valid, unsigned char* smem_raw) {
+    static_assert(!RefSub<T>::on, "component-parallel bodies assume no reference subtraction");
+    using Tl = Tile<NP>;
+    constexpr int P = Tl::P, S2 = Tl::S2;
+    T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)el * (tiles_per_elem<2>(OP_JACT) + 1) * S2;
+    T* sU[2] = {sm, sm + S2};
+    T* sZ[2] = {sm + 2 * S2, sm + 3 * S2};
+    T* sF = sm + (4 + l) * S2;
+    const int ex = e % a.E, ey = e / a.E;
+    load2<T, NP>(sU[l], a.u, l, ex, ey, t, valid, a, false);
+    load2<T, NP>(sZ[l], a.w, l, ex, ey, t, valid, a, true);
+    __syncthreads();
+    const T rU[2] = {(T)0, (T)0};
+    const int xb = t * P, yb = t;
+    auto* out = reinterpret_cast<typename OutT<T>::type*>(a.lvec) + (size_t)e * 2 * (NP * NP) + (size_t)l * NP * NP + t;
+    T r[NP];
+    jact_pass<T, NP, 1, 2>(M, sU, sZ, rU, l, 0, xb, r);
+    st_line<T, NP, 1>(sF, xb, r);
+    __syncthreads();
+    jact_pass<T, NP, P, 2>(M, sU, sZ, rU, l, 1, yb, r);
+    if (valid) {
+#pragma unroll
+        for (int m = 0; m < NP; ++m) out[m * NP] = to_out(r[m] + sF[yb + m * P]);
+    }
+}
+
+// Block of elements; thread (t, c) = (threadIdx.x % n, (threadIdx.x / n) % 2) of element slot threadIdx.x / 2n.
+template <typename T, int NP>
+__global__ void __launch_bounds__(256, 2) op2c_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a, int op) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int el = threadIdx.x / (2 * NP), t = threadIdx.x % NP, c = (threadIdx.x / NP) % 2;
+    const int e = blockIdx.x * (blockDim.x / (2 * NP)) + el;
+    const bool valid = e < a.nelem;
+    if (op == OP_RHS) rhs2c_body<T, NP>(M, a, e, t, c, el, valid, smem_raw);
+    else if (op == OP_JAC) jac2c_body<T, NP>(M, a, e, t, c, el, valid, smem_raw);
+    else jact2c_body<T, NP>(M, a, e, t, c, el, valid, smem_raw);
+}
+
 // ================================================================== d = 1
 // One thread per element; everything in registers.
 template <typename T, int NP>

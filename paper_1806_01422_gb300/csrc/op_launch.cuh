@@ -28,10 +28,17 @@ void split_eo(EOMat<T, NP>& M, const double* A) {
 constexpr int SMEM_TARGET = 100 * 1024;   // two blocks per SM fit in 227 KB
 constexpr int NUM_SMS = 152;               // GB300: 2 dies x 76 SMs
 
+// 2D double-float kernels run one thread per (line, component) (op2c_kernel)
+template <typename T, int D>
+__host__ __device__ constexpr bool comp_parallel() {
+    return D == 2 && std::is_same<T, dfloat>::value;
+}
+
 template <typename T, int D, int NP>
 size_t elem_smem_bytes(int op) {
     using Tl = Tile<NP>;
     const size_t tile = D == 3 ? Tl::S3 : (D == 2 ? Tl::S2 : 0);
+    if (comp_parallel<T, D>()) return (size_t)(tiles_per_elem<D>(op) + 1) * tile * sizeof(T);
     if (D == 3 && lean3<T, NP>()) return (size_t)lean_tiles_per_elem<D>(op) * tile * sizeof(T);
     return (size_t)tiles_per_elem<D>(op) * tile * sizeof(T);
 }
@@ -50,7 +57,7 @@ cudaError_t launch_elem_np(int op, const double* mats, const ElemArgs& a, cudaSt
         op1_kernel<T, NP><<<blocks, threads, 0, s>>>(M, a, op);
         return cudaGetLastError();
     } else {
-        constexpr int TPE = D == 3 ? NP * NP : NP;
+        constexpr int TPE = D == 3 ? NP * NP : (comp_parallel<T, D>() ? 2 * NP : NP);
         constexpr bool lean = D == 3 && lean3<T, NP>();
         const size_t per = elem_smem_bytes<T, D, NP>(op);
         const int epb_max = lean ? 1 : std::max(1, std::min(256 / TPE, (int)(SMEM_TARGET / per)));
@@ -63,6 +70,24 @@ cudaError_t launch_elem_np(int op, const double* mats, const ElemArgs& a, cudaSt
         if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
         const int threads = epb * TPE;
         const int blocks = (a.nelem + epb - 1) / epb;
+        if constexpr (comp_parallel<T, D>()) {
+            if (smem > 48 * 1024) {
+                static thread_local unsigned long long done_c = 0;
+                static thread_local size_t done_c_smem = 0;
+                int dev = 0;
+                cudaGetDevice(&dev);
+                const unsigned long long bit = 1ull << (dev & 63);
+                if (!(done_c & bit) || done_c_smem < smem) {
+                    cudaError_t err = cudaFuncSetAttribute(op2c_kernel<T, NP>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    if (err != cudaSuccess) return err;
+                    done_c |= bit;
+                    done_c_smem = smem;
+                }
+            }
+            op2c_kernel<T, NP><<<blocks, threads, smem, s>>>(M, a, op);
+            return cudaGetLastError();
+        }
         void (*k)(const OpMats<T, NP>, const ElemArgs);
         if constexpr (lean)
             k = op == OP_RHS ? rhs3_lean_kernel<T, NP>

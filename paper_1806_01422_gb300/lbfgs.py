@@ -97,6 +97,9 @@ def more_thuente(phi, f0, g0, stp=1.0, ftol=1e-4, gtol=0.9, xtol=1e-10, stpmin=1
     """Step satisfying the strong Wolfe conditions for phi(t) = f(x + t d).
 
     phi(t) returns (f, derivative along d, payload); f0, g0 at t = 0 (g0 < 0).
+    A trial step whose f or derivative is not finite (the model left its range of
+    validity) becomes the new upper limit of the step and the next trial moves
+    halfway back towards the best step so far.
     Returns (t, f, payload, evaluations).
     """
     if g0 >= 0.0:
@@ -116,6 +119,10 @@ def more_thuente(phi, f0, g0, stp=1.0, ftol=1e-4, gtol=0.9, xtol=1e-10, stpmin=1
         if brackt and (stp <= stmin or stp >= stmax or stmax - stmin <= xtol * stmax):
             stp = stx
         f, g, payload = phi(stp)
+        if not (math.isfinite(f) and math.isfinite(g)):
+            stpmax = stp
+            stp = stx + 0.5 * (stp - stx)
+            continue
         if best is None or f < best[1]:
             best = (stp, f, payload)
         ftest = f0 + stp * gtest
@@ -140,15 +147,22 @@ def more_thuente(phi, f0, g0, stp=1.0, ftol=1e-4, gtol=0.9, xtol=1e-10, stpmin=1
             if abs(sty - stx) >= 0.66 * width1:
                 stp = stx + 0.5 * (sty - stx)
             width1, width = width, abs(sty - stx)
+    if best is None:
+        raise FloatingPointError("no finite function value along the search direction")
     return best[0], best[1], best[2], maxfev
 
 
-def lbfgs(fg, x0, m=8, max_iter=30, gtol=1e-8, callback=None, line_search_maxfev=20):
+def lbfgs(fg, x0, m=8, max_iter=30, gtol=1e-8, callback=None, line_search_maxfev=20, h0_diag=None):
     """Minimise f with L-BFGS (two-loop recursion) and the Moré-Thuente line search.
 
     fg(x) -> (f, grad); x0: tensor.  Returns (x, history) where history holds
     (iteration, f, |grad|, function evaluations).  Stops after max_iter
     iterations or when |grad| <= gtol |grad_0|.
+
+    h0_diag: optional diagonal of the initial inverse Hessian H_0 (a tensor like x).
+    Without it H_0 = gamma I (Nocedal & Wright eq. 7.20) and the first step is a unit
+    step along -grad / |grad|; with it H_0 = gamma D, gamma = s^T y / y^T D y, and the
+    first direction is -D grad (a preconditioned, scale-aware quasi-Newton method).
     """
     x = x0.clone()
     f, g = fg(x)
@@ -165,7 +179,11 @@ def lbfgs(fg, x0, m=8, max_iter=30, gtol=1e-8, callback=None, line_search_maxfev
             a = r * _dot(s, q)
             alpha.append(a)
             q.add_(y, alpha=-a)
-        if S:
+        if h0_diag is not None:
+            q.mul_(h0_diag)
+            if S:
+                q.mul_(_dot(S[-1], Y[-1]) / _dot(Y[-1], h0_diag * Y[-1]))
+        elif S:
             gamma = _dot(S[-1], Y[-1]) / _dot(Y[-1], Y[-1])
             q.mul_(gamma)
         else:
@@ -175,14 +193,16 @@ def lbfgs(fg, x0, m=8, max_iter=30, gtol=1e-8, callback=None, line_search_maxfev
             q.add_(s, alpha=a - b)
         d = -q
         dg = _dot(d, g)
-        if dg >= 0.0:               # not a descent direction: restart from steepest descent
+        if dg >= 0.0:               # not a descent direction: restart from (scaled) steepest descent
             S, Y, rho = [], [], []
-            d = -g / max(math.sqrt(_dot(g, g)), 1e-300)
+            d = -(g * h0_diag) if h0_diag is not None else -g / max(math.sqrt(_dot(g, g)), 1e-300)
             dg = _dot(d, g)
 
         def phi(t):
             xt = x + t * d
             ft, gt = fg(xt)
+            if gt is None or not math.isfinite(ft):
+                return math.inf, math.nan, None
             gt = gt.clone()
             return ft, _dot(gt, d), (xt, gt)
 

@@ -1,4 +1,6 @@
 """L-BFGS with the Moré-Thuente line search on problems with known minimisers (CPU)."""
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -34,3 +36,25 @@ def test_rosenbrock_converges():
         return float(f), g
     x, hist = lbfgs(fg, torch.tensor([-1.2, 1.0], dtype=torch.float64), m=6, max_iter=200, gtol=1e-10)
     assert torch.allclose(x, torch.tensor([1.0, 1.0], dtype=torch.float64), atol=1e-6)
+
+
+def test_line_search_backs_off_from_non_finite_values():
+    """f(t) is only finite for t < 0.3 along the direction: the search must shrink into that range."""
+    def phi(t):
+        if t >= 0.3:
+            return math.inf, math.nan, None
+        return (t - 0.2) ** 2, 2.0 * (t - 0.2), t
+    t, f, payload, nfev = more_thuente(phi, 0.04, -0.4, stp=1.0)
+    assert t < 0.3 and f < 0.04 and payload == t
+
+
+def test_diagonal_initial_hessian_solves_a_badly_scaled_quadratic_at_once():
+    """f = 1/2 sum a_i x_i^2 with a_i spread over four decades: with H_0 = diag(1/a) the first
+    direction is the Newton step, so the unit step lands on the minimiser."""
+    a = torch.logspace(0, 4, 50, dtype=torch.float64)
+    x0 = torch.ones(50, dtype=torch.float64)
+    fg = lambda x: (0.5 * float((a * x * x).sum()), a * x)
+    x, hist = lbfgs(fg, x0, max_iter=3, h0_diag=1.0 / a)
+    assert hist[1][1] < 1e-28 and float(x.abs().max()) < 1e-14
+    _, plain = lbfgs(fg, x0, max_iter=3)
+    assert plain[-1][1] > 1e-6          # the unscaled method is still far off after 3 iterations
