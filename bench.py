@@ -78,7 +78,7 @@ TRAFFIC = {
         "bytes": 6477568 + 0, "src": "4614f8cb473058eb",
         "capture": "dram__bytes_read.sum + dram__bytes_write.sum of one jact2 launch at 64x64 quads, N=7 "
                    "(ncu --set full; profiles/rhs2_jact2_assemble_2d_fp64_E64_N7.md)"},
-    "jact2_kernel<semk::dfa::dfloat,8>@2d@fp64_df": {
+    "op2c_kernel<semk::dfa::dfloat,8> (J^T)@2d@fp64_df": {
         "bytes": 6573056 + 0, "src": "4614f8cb473058eb",
         "capture": "dram__bytes_read.sum + dram__bytes_write.sum of one J^T launch (op2c_kernel) at 64x64 "
                    "quads, N=7 (ncu --set full; profiles/rhs2_jact2_2d_fp64df_E64_N7.md)"},
@@ -299,8 +299,11 @@ def roofline_of(prof, args, w, s, precision):
         dfk = precision == "fp64_df"
         peak = PEAK_FP32_TFLOPS if fp32 else (PEAK_DF_TFLOPS if dfk else PEAK_FP64_TFLOPS)
         ctype = "float" if fp32 else ("semk::dfa::dfloat" if dfk else "double")
+        kernel = kname or "%s%d_kernel<%s,%d>" % (names[dom], w["dim"], ctype, w["N"] + 1)
+        if dfk and w["dim"] == 2:
+            kernel = "op2c_kernel<%s,%d> (%s)" % (ctype, w["N"] + 1, {"rhs": "F", "jac": "J", "jacT": "J^T"}[dom])
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "kernel": kname or "%s%d_kernel<%s,%d>" % (names[dom], w["dim"], ctype, w["N"] + 1)}
+                "kernel": kernel}
         if dfk:
             roof["peak_note"] = ("double-float multiply-add rate of the FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz "
                                  "/ 13 FP32 operations per multiply-add, x 2 flop")

@@ -505,6 +505,35 @@ __device__ __forceinline__ void jac2c_body(const OpMats<T, NP>& M, const ElemArg
     }
 }
 
+// J^T pass with the line stride as a run-time value: the x and y passes of
+// jact2c_body then share one copy of the code.  The fully unrolled double-float
+// passes are long straight-line code, and two copies of them overflow the
+// instruction cache once the warps of an SM drift apart.
+template <typename T, int NP, int D>
+__device__ __forceinline__ void jact_pass_rt(const OpMats<T, NP>& M, T* const* sU, T* const* sZ, const T* rU, int l,
+                                             int d, int base, int stride, T (&r)[NP]) {
+    T z[NP], q[NP], dv[NP];
+#pragma unroll
+    for (int m = 0; m < NP; ++m) z[m] = sZ[l][base + m * stride];
+    eo_apply<true, T, NP>(M.Svt, z, r);
+#pragma unroll
+    for (int m = 0; m < NP; ++m) q[m] = with_ref(rU[d], sU[d][base + m * stride]) * z[m];
+    eo_apply<false, T, NP>(M.Dd, q, dv);
+#pragma unroll
+    for (int m = 0; m < NP; ++m) r[m] += dv[m];
+    if (l == d) {
+#pragma unroll 1
+        for (int c = 0; c < D; ++c) {
+            T x[NP], g[NP];
+#pragma unroll
+            for (int m = 0; m < NP; ++m) x[m] = sU[c][base + m * stride];
+            eo_apply<false, T, NP>(M.Dg, x, g);
+#pragma unroll
+            for (int m = 0; m < NP; ++m) r[m] = fma(-sZ[c][base + m * stride], g[m], r[m]);
+        }
+    }
+}
+
 template <typename T, int NP>
 __device__ __forceinline__ void jact2c_body(const OpMats<T, NP>& M, const ElemArgs& a, int e, int t, int l, int el,
                                           bool valid, unsigned char* smem_raw) {
@@ -522,23 +551,30 @@ __device__ __forceinline__ void jact2c_body(const OpMats<T, NP>& M, const ElemAr
     const T rU[2] = {(T)0, (T)0};
     const int xb = t * P, yb = t;
     auto* out = reinterpret_cast<typename OutT<T>::type*>(a.lvec) + (size_t)e * 2 * (NP * NP) + (size_t)l * NP * NP + t;
-    T r[NP];
-    jact_pass<T, NP, 1, 2>(M, sU, sZ, rU, l, 0, xb, r);
-    st_line<T, NP, 1>(sF, xb, r);
-    __syncthreads();
-    jact_pass<T, NP, P, 2>(M, sU, sZ, rU, l, 1, yb, r);
-    if (valid) {
+#pragma unroll 1
+    for (int d = 0; d < 2; ++d) {
+        T r[NP];
+        jact_pass_rt<T, NP, 2>(M, sU, sZ, rU, l, d, d ? yb : xb, d ? P : 1, r);
+        if (d == 0) {
+            st_line<T, NP, 1>(sF, xb, r);
+            __syncthreads();
+        } else if (valid) {
 #pragma unroll
-        for (int m = 0; m < NP; ++m) out[m * NP] = to_out(r[m] + sF[yb + m * P]);
+            for (int m = 0; m < NP; ++m) out[m * NP] = to_out(r[m] + sF[yb + m * P]);
+        }
     }
 }
 
-// Block of elements; thread (t, c) = (threadIdx.x % n, (threadIdx.x / n) % 2) of element slot threadIdx.x / 2n.
+// Block of epb elements: the first half of the block runs component 0 of every
+// element, the second half component 1, so that a warp takes one branch of the
+// J^T cross term (the launcher makes epb n a multiple of 32 where it can).
 template <typename T, int NP>
 __global__ void __launch_bounds__(256, 2) op2c_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a, int op) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int el = threadIdx.x / (2 * NP), t = threadIdx.x % NP, c = (threadIdx.x / NP) % 2;
-    const int e = blockIdx.x * (blockDim.x / (2 * NP)) + el;
+    const int half = blockDim.x / 2;
+    const int c = threadIdx.x >= half, r = threadIdx.x - c * half;
+    const int el = r / NP, t = r % NP;
+    const int e = blockIdx.x * (half / NP) + el;
     const bool valid = e < a.nelem;
     if (op == OP_RHS) rhs2c_body<T, NP>(M, a, e, t, c, el, valid, smem_raw);
     else if (op == OP_JAC) jac2c_body<T, NP>(M, a, e, t, c, el, valid, smem_raw);

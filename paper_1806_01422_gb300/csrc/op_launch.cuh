@@ -66,6 +66,14 @@ cudaError_t launch_elem_np(int op, const double* mats, const ElemArgs& a, cudaSt
         const int waves = (a.nelem + NUM_SMS * epb_max - 1) / (NUM_SMS * epb_max);
         int epb = (a.nelem + NUM_SMS * waves - 1) / (NUM_SMS * waves);
         epb = std::max(1, std::min(epb, epb_max));
+        if constexpr (comp_parallel<T, D>()) {
+            // warp-aligned halves: epb * n a multiple of 32 when that fits
+            int g = 32, n = NP;
+            while (n) { const int r = g % n; g = n; n = r; }
+            const int step = 32 / g;
+            const int up = (epb + step - 1) / step * step;
+            if (up <= epb_max) epb = up;
+        }
         const size_t smem = per * epb;
         if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
         const int threads = epb * TPE;
