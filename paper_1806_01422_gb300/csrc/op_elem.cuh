@@ -198,6 +198,95 @@ __device__ __forceinline__ void jact_pass(const OpMats<T, NP>& M, T* const* sU, 
     }
 }
 
+// 3D kernels that run their passes from one copy of the code (df3_body): the
+// double-float ones (long unrolled passes) and FP32 with n >= 12 (register-bound
+// with three unrolled copies).
+template <typename T, int NP>
+__host__ __device__ constexpr bool shared_pass3() {
+    return std::is_same<T, dfloat>::value || (sizeof(T) == 4 && NP >= 12);
+}
+
+template <typename T, int NP, int D>
+__device__ __forceinline__ void jact_pass_rt(const OpMats<T, NP>& M, T* const* sU, T* const* sZ, const T* rU, int l,
+                                             int d, int base, int stride, T (&r)[NP]);
+
+// Run-time-stride versions of the passes, for the double-float kernels: one copy of
+// a pass serves every direction (see jact_pass_rt).
+template <typename T, int NP>
+__device__ __forceinline__ void rhs_pass_rt(const OpMats<T, NP>& M, const T* sUc, const T* sUd, T rd, int base,
+                                            int stride, T (&r)[NP]) {
+    T x[NP], g[NP];
+#pragma unroll
+    for (int m = 0; m < NP; ++m) x[m] = sUc[base + m * stride];
+    Pre<T, NP> p;
+    pre_add<T, NP>(x, p);
+    eo_apply<false, T, NP>(M.Dg, p, g);
+    eo_apply<true, T, NP>(M.Sv, p, r);
+#pragma unroll
+    for (int m = 0; m < NP; ++m) r[m] = fma(-with_ref(rd, sUd[base + m * stride]), g[m], r[m]);
+}
+
+template <typename T, int NP>
+__device__ __forceinline__ void jac_pass_rt(const OpMats<T, NP>& M, const T* sUc, const T* sWc, const T* sUd,
+                                            const T* sWd, T ru, T rw, int base, int stride, T (&r)[NP]) {
+    T x[NP], gw[NP], gu[NP];
+#pragma unroll
+    for (int m = 0; m < NP; ++m) x[m] = sWc[base + m * stride];
+    Pre<T, NP> p;
+    pre_add<T, NP>(x, p);
+    eo_apply<false, T, NP>(M.Dg, p, gw);
+    eo_apply<true, T, NP>(M.Sv, p, r);
+#pragma unroll
+    for (int m = 0; m < NP; ++m) x[m] = sUc[base + m * stride];
+    eo_apply<false, T, NP>(M.Dg, x, gu);
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+        const int id = base + m * stride;
+        r[m] -= fma(with_ref(rw, sWd[id]), gu[m], with_ref(ru, sUd[id]) * gw[m]);
+    }
+}
+
+// d = 3 double-float element body: the three passes run from one copy of the pass
+// code in a loop over directions; x and y write the partial tiles, z adds and stores.
+template <typename T, int NP>
+__device__ __forceinline__ void df3_body(const OpMats<T, NP>& M, const ElemArgs& a, int op, T* const* sU,
+                                         T* const* sV, T* sF, T* sA, const T* rU, const T* rV, int e, int t,
+                                         bool valid) {
+    using Tl = Tile<NP>;
+    constexpr int P = Tl::P, S2 = Tl::S2;
+    const int xb = t * P, yb = (t / NP) * S2 + t % NP, zb = (t / NP) * P + t % NP;
+    auto* out = reinterpret_cast<typename OutT<T>::type*>(a.lvec) + (size_t)e * 3 * (NP * NP * NP) + (t / NP) * NP + t % NP;
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll 1
+        for (int d = 0; d < 3; ++d) {
+            const int base = d == 0 ? xb : (d == 1 ? yb : zb);
+            const int stride = d == 0 ? 1 : (d == 1 ? P : S2);
+            const T* sUd = d == 0 ? sU[0] : (d == 1 ? sU[1] : sU[2]);
+            T r[NP];
+            if (op == OP_RHS) {
+                rhs_pass_rt<T, NP>(M, sU[c], sUd, rU[d], base, stride, r);
+            } else if (op == OP_JAC) {
+                const T* sVd = d == 0 ? sV[0] : (d == 1 ? sV[1] : sV[2]);
+                jac_pass_rt<T, NP>(M, sU[c], sV[c], sUd, sVd, rU[d], rV[d], base, stride, r);
+            } else {
+                jact_pass_rt<T, NP, 3>(M, sU, sV, rU, c, d, base, stride, r);
+            }
+            if (d < 2) {
+                T* dst = d == 0 ? sF : sA;
+#pragma unroll
+                for (int m = 0; m < NP; ++m) dst[base + m * stride] = r[m];
+                if (d == 1) __syncthreads();
+            } else if (valid) {
+#pragma unroll
+                for (int m = 0; m < NP; ++m)
+                    out[(size_t)c * NP * NP * NP + m * NP * NP] = to_out(r[m] + (sF[zb + m * S2] + sA[zb + m * S2]));
+            }
+        }
+        __syncthreads();
+    }
+}
+
 template <typename T, int NP>
 __global__ void rhs3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
     using Tl = Tile<NP>;
@@ -215,6 +304,10 @@ __global__ void rhs3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
 #pragma unroll
     for (int c = 0; c < 3; ++c) rU[c] = load3<T, NP>(sU[c], a.u, c, ex, ey, ez, t, valid, a, false);
     __syncthreads();
+    if constexpr (shared_pass3<T, NP>()) {
+        df3_body<T, NP>(M, a, OP_RHS, sU, sU, sF, sA, rU, rU, e, t, valid);
+        return;
+    }
     const int xb = t * P, yb = (t / NP) * S2 + t % NP, zb = (t / NP) * P + t % NP;
     auto* out = reinterpret_cast<typename OutT<T>::type*>(a.lvec) + (size_t)e * 3 * (NP * NP * NP) + (t / NP) * NP + t % NP;
 #pragma unroll 1
@@ -255,6 +348,10 @@ __global__ void jac3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
         rW[c] = load3<T, NP>(sW[c], a.w, c, ex, ey, ez, t, valid, a, false);
     }
     __syncthreads();
+    if constexpr (shared_pass3<T, NP>()) {
+        df3_body<T, NP>(M, a, OP_JAC, sU, sW, sF, sA, rU, rW, e, t, valid);
+        return;
+    }
     const int xb = t * P, yb = (t / NP) * S2 + t % NP, zb = (t / NP) * P + t % NP;
     auto* out = reinterpret_cast<typename OutT<T>::type*>(a.lvec) + (size_t)e * 3 * (NP * NP * NP) + (t / NP) * NP + t % NP;
 #pragma unroll 1
@@ -295,6 +392,10 @@ __global__ void jact3_kernel(const __grid_constant__ OpMats<T, NP> M, const Elem
         load3<T, NP>(sZ[c], a.w, c, ex, ey, ez, t, valid, a, true);
     }
     __syncthreads();
+    if constexpr (shared_pass3<T, NP>()) {
+        df3_body<T, NP>(M, a, OP_JACT, sU, sZ, sF, sA, rU, rU, e, t, valid);
+        return;
+    }
     const int xb = t * P, yb = (t / NP) * S2 + t % NP, zb = (t / NP) * P + t % NP;
     auto* out = reinterpret_cast<typename OutT<T>::type*>(a.lvec) + (size_t)e * 3 * (NP * NP * NP) + (t / NP) * NP + t % NP;
 #pragma unroll 1

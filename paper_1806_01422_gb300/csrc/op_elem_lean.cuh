@@ -1,8 +1,8 @@
-// Element kernels of d = 3 for FP64 with many points per direction (n >= 13):
-// the same passes as rhs3/jac3/jact3 (op_elem.cuh) with fewer shared-memory
-// tiles, so that one element's tiles fit the 227 KB of an SM.  With n = 16 the
-// plain kernels would need 5 tiles of 16 x 16 x 17 doubles (174 KB) for F and 8
-// (278 KB) for J and J^T.
+// Element kernels of d = 3 with many points per direction (n >= 13): the same
+// passes as rhs3/jac3/jact3 (op_elem.cuh) with fewer shared-memory tiles.  In
+// FP64 this is what makes one element's tiles fit the 227 KB of an SM (with
+// n = 16 the plain kernels would need 5 tiles of 16 x 16 x 17 doubles, 174 KB,
+// for F and 8, 278 KB, for J and J^T); in FP32 it lets two blocks share an SM.
 //
 //  * One element per block (n^2 threads).
 //  * F: the x and y passes accumulate into one partial tile (an extra barrier
@@ -22,13 +22,17 @@ namespace semk {
 
 template <typename T, int NP>
 __host__ __device__ constexpr bool lean3() {
-    return sizeof(T) == 8 && NP >= 13;
+    return NP >= 13;
 }
 
 template <int D>
 __host__ __device__ constexpr int lean_tiles_per_elem(int op) {
     return op == OP_RHS ? D + 1 : 2 * D;
 }
+
+template <typename T, int NP>
+__device__ __forceinline__ void df3_lean_body(const OpMats<T, NP>& M, const ElemArgs& a, int op, T* const* sU,
+                                              T* const* sV, T* sF, const T* rU, const T* rV, int e, int t);
 
 template <typename T, int NP>
 __global__ void __launch_bounds__(NP * NP)
@@ -46,6 +50,10 @@ rhs3_lean_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) rU[c] = load3<T, NP>(sU[c], a.u, c, ex, ey, ez, t, true, a, false);
     __syncthreads();
+    if constexpr (shared_pass3<T, NP>()) {
+        df3_lean_body<T, NP>(M, a, OP_RHS, sU, sU, sF, rU, rU, e, t);
+        return;
+    }
     const int xb = t * P, yb = (t / NP) * S2 + t % NP, zb = (t / NP) * P + t % NP;
     auto* out = reinterpret_cast<typename OutT<T>::type*>(a.lvec) + (size_t)e * 3 * (NP * NP * NP) + (t / NP) * NP + t % NP;
 #pragma unroll 1
@@ -92,6 +100,52 @@ __device__ __forceinline__ void lean_add_z(O* o, int t, const T (&r)[NP]) {
     for (int m = 0; m < NP; ++m) p[m * NP * NP] += to_out(r[m]);
 }
 
+// Double-float lean body: the three passes from one copy of the pass code (see
+// df3_body); F keeps its partial sum in one tile, J and J^T in the output.
+template <typename T, int NP>
+__device__ __forceinline__ void df3_lean_body(const OpMats<T, NP>& M, const ElemArgs& a, int op, T* const* sU,
+                                              T* const* sV, T* sF, const T* rU, const T* rV, int e, int t) {
+    using Tl = Tile<NP>;
+    constexpr int P = Tl::P, S2 = Tl::S2;
+    const int xb = t * P, yb = (t / NP) * S2 + t % NP, zb = (t / NP) * P + t % NP;
+    auto* out = reinterpret_cast<typename OutT<T>::type*>(a.lvec) + (size_t)e * 3 * (NP * NP * NP);
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        auto* oc = out + (size_t)c * NP * NP * NP;
+#pragma unroll 1
+        for (int d = 0; d < 3; ++d) {
+            const int base = d == 0 ? xb : (d == 1 ? yb : zb);
+            const int stride = d == 0 ? 1 : (d == 1 ? P : S2);
+            const T* sUd = d == 0 ? sU[0] : (d == 1 ? sU[1] : sU[2]);
+            T r[NP];
+            if (op == OP_RHS) {
+                rhs_pass_rt<T, NP>(M, sU[c], sUd, rU[d], base, stride, r);
+                if (d == 0) {
+#pragma unroll
+                    for (int m = 0; m < NP; ++m) sF[base + m * stride] = r[m];
+                } else if (d == 1) {
+#pragma unroll
+                    for (int m = 0; m < NP; ++m) sF[base + m * stride] += r[m];
+                } else {
+#pragma unroll
+                    for (int m = 0; m < NP; ++m) oc[(t / NP) * NP + t % NP + m * NP * NP] = to_out(r[m] + sF[zb + m * S2]);
+                }
+            } else {
+                if (op == OP_JAC) {
+                    const T* sVd = d == 0 ? sV[0] : (d == 1 ? sV[1] : sV[2]);
+                    jac_pass_rt<T, NP>(M, sU[c], sV[c], sUd, sVd, rU[d], rV[d], base, stride, r);
+                } else {
+                    jact_pass_rt<T, NP, 3>(M, sU, sV, rU, c, d, base, stride, r);
+                }
+                if (d == 0) lean_out_x<T, NP>(oc, t, r);
+                else if (d == 1) lean_add_y<T, NP>(oc, t, r);
+                else lean_add_z<T, NP>(oc, t, r);
+            }
+            __syncthreads();
+        }
+    }
+}
+
 template <typename T, int NP>
 __global__ void __launch_bounds__(NP * NP)
 jac3_lean_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
@@ -111,6 +165,10 @@ jac3_lean_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
         rW[c] = load3<T, NP>(sW[c], a.w, c, ex, ey, ez, t, true, a, false);
     }
     __syncthreads();
+    if constexpr (shared_pass3<T, NP>()) {
+        df3_lean_body<T, NP>(M, a, OP_JAC, sU, sW, nullptr, rU, rW, e, t);
+        return;
+    }
     const int xb = t * P, yb = (t / NP) * S2 + t % NP, zb = (t / NP) * P + t % NP;
     auto* out = reinterpret_cast<typename OutT<T>::type*>(a.lvec) + (size_t)e * 3 * (NP * NP * NP);
 #pragma unroll 1
@@ -147,6 +205,10 @@ jact3_lean_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
         load3<T, NP>(sZ[c], a.w, c, ex, ey, ez, t, true, a, true);
     }
     __syncthreads();
+    if constexpr (shared_pass3<T, NP>()) {
+        df3_lean_body<T, NP>(M, a, OP_JACT, sU, sZ, nullptr, rU, rU, e, t);
+        return;
+    }
     const int xb = t * P, yb = (t / NP) * S2 + t % NP, zb = (t / NP) * P + t % NP;
     auto* out = reinterpret_cast<typename OutT<T>::type*>(a.lvec) + (size_t)e * 3 * (NP * NP * NP);
 #pragma unroll 1

@@ -297,3 +297,26 @@ def test_kernel_timing_inside_a_replayed_graph():
     assert second["rhs"][1] == 6 and second["jacT"][1] == 6 and second["assemble"][1] == 12
     assert first["rhs"][1] == second["rhs"][1]
     assert all(second[k][0] > 0 for k in ("rhs", "jacT", "assemble"))
+
+
+# Degenerate cases: the lowest order (two points per direction), no viscosity, the zero field.
+@pytest.mark.parametrize("prec", ["fp64", "fp64_df"])
+@pytest.mark.parametrize("dim,E,N", [(1, 4, 1), (2, 3, 1), (3, 2, 1), (2, 5, 2)])
+def test_lowest_orders_match_oracle(dim, E, N, prec):
+    s, g = Sem(dim, E, N, 0.037, precision=prec), Grid(dim, E, N, 0.037)
+    u, w = inputs.field_random(dim, g.G, 30 + dim), inputs.field_random(dim, g.G, 40 + dim)
+    assert relerr(s.rhs(u), g.rhs(u)) < RTOL64
+    assert relerr(s.jac(u, w), g.jac(u, w)) < RTOL64
+    assert relerr(s.jacT(u, w), g.jacT(u, w)) < RTOL64
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp64_df", "fp32_bulk"])
+def test_inviscid_and_zero_fields(prec):
+    s, g = Sem(2, 4, 5, 0.0, precision=prec), Grid(2, 4, 5, 0.0)
+    u, w = smooth(g, 1), smooth(g, 2)
+    tol = RTOL32 if prec == "fp32_bulk" else RTOL64
+    assert relerr(s.rhs(u), g.rhs(u)) < tol
+    assert relerr(s.jacT(u, w), g.jacT(u, w)) < tol
+    z = np.zeros_like(u)
+    assert float(s.rhs(z).abs().max()) == 0.0          # F(0) = 0 exactly
+    assert float(s.jacT(z, z).abs().max()) == 0.0
