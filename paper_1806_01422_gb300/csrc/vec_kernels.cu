@@ -26,6 +26,16 @@ __device__ __forceinline__ bool nonfinite_bits(double v) {
     return (__double2hiint(v) & 0x7ff00000) == 0x7ff00000;
 }
 
+// alpha_k[o][nsh] of a kernel-parameter table, picked with selects on the four
+// statically addressed entries: an indexed parameter load would be a
+// dependent constant-cache access on the path of every thread.
+template <typename A>
+__device__ __forceinline__ A pick4(const A (&t)[4], int k) {
+    const A lo = k & 1 ? t[1] : t[0];
+    const A hi = k & 1 ? t[3] : t[2];
+    return k & 2 ? hi : lo;
+}
+
 // The launch grid is (ceil(G / 128), G, d) for d = 2 and (ceil(G / 128), G, d G)
 // for d = 3, so a thread finds its node without integer division (32-bit
 // division and modulo issue conversion instructions on the FP64 pipe); the
@@ -95,7 +105,7 @@ __global__ void __launch_bounds__(128) assemble_kernel(const T* __restrict__ lve
     bool bad = false;
 #pragma unroll
     for (int o = 0; o < NOUT; ++o) {
-        double v = ep.alpha_k[o][nsh] * sumd;
+        double v = pick4(ep.alpha_k[o], nsh) * sumd;
 #pragma unroll
         for (int m = 0; m < NSRC; ++m) v = fma(ep.beta[o][m], sv[m], v);
         ov[o] = v;
@@ -182,7 +192,7 @@ __global__ void __launch_bounds__(128) assemble_f32_kernel(const float* __restri
         bool bad = false;
 #pragma unroll
         for (int o = 0; o < NOUT; ++o) {
-            df v = df_mul_f(ep.alpha_k[o][nsh], sum);
+            df v = df_mul_f(pick4(ep.alpha_k[o], nsh), sum);
 #pragma unroll
             for (int m = 0; m < NSRC; ++m) v = df_add(v, df_mul(ep.beta[o][m], sv[m]));
             ov[o] = v;
