@@ -429,8 +429,12 @@ def gpu_arm(args, world, rank, local):
     st = s.sweep_stats()
     elapsed = e0.elapsed_time(e1) / 1e3
     value, tmax = job_value(elapsed, args.steps * units, world, dev)
-    # element kernel + assembly per apply, plus misfit, partial sum and adjoint seed per step
-    launches = args.steps * (2 * (st["forward_rhs"] + st["adjoint_rhs"] + st["adjoint_jacT"]) + 3)
+    # element kernels and assemblies (counted by the library; fused assemblies are not
+    # launches), plus misfit, partial sum and adjoint seed per step
+    if args.workload == "batch":
+        launches = args.steps * (2 * (st["forward_rhs"] + st["adjoint_rhs"] + st["adjoint_jacT"]) + 3)
+    else:
+        launches = args.steps * (s.launch_count() + 3)
     if scheme == "cn":
         # per Arnoldi step 5 two-kernel dot passes, 2 axpys and a scale; per GMRES solve a norm, a
         # scale and the update; per Newton iteration the update and two norms
