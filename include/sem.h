@@ -194,20 +194,6 @@ int sem_sweep_stats(sem_t h, long long* out3);
  * forward sweep and any recorded gradient graph. */
 int sem_set_advection(sem_t h, const double* a, void* stream);
 
-/* Fused gather-scatter (off by default; no counterpart in the paper).  With
- * enable != 0, inside the RK forward and adjoint sweeps of FP64 and FP64-DF
- * single-instance handles (d = 2, 3; d = 3 up to N = 11), the gather-scatter
- * sum and stage epilogue of every stage but the last of a step is not launched
- * on its own: the next stage's element kernel forms the assembled values of its
- * element's nodes while loading them (same contributions, same order, same
- * arithmetic) and the element holding a node at local indices < N writes the
- * epilogue's outputs there.  Results are the same bits either way.  On GB300
- * the 2D workload ran slower fused (1.58 against 1.79 gradient evaluations/s
- * in FP64): the element kernels run one block per SM, so the longer gather in
- * their load phase is not hidden behind other blocks' arithmetic.  Host-only;
- * discards a recorded gradient graph. */
-int sem_set_fusion(sem_t h, int enable);
-
 /* Element-kernel and assembly launches made by operator applies since the last
  * forward sweep began (its adjoint sweep included; a recorded gradient graph
  * replays the launches counted while it was recorded).  Host-only. */

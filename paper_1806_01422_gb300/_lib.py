@@ -58,7 +58,6 @@ _SIGS = {
     "sem_set_advection": (_I, [_H, _P, _P]),
     "sem_set_host_tier": (_I, [_H, ctypes.c_size_t]),
     "sem_set_adaptive": (_I, [_H, _D, _D]),
-    "sem_set_fusion": (_I, [_H, _I]),
     "sem_launch_count": (_I, [_H, ctypes.POINTER(ctypes.c_longlong)]),
     "sem_adaptive_steps": (_I, [_H, ctypes.POINTER(_I), ctypes.POINTER(_I), _P, _I]),
     "sem_trajectory_info": (_I, [_H, ctypes.POINTER(ctypes.c_longlong)]),

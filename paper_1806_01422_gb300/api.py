@@ -167,10 +167,6 @@ class Sem:
         L.check(L.lib().sem_launch_count(self._h, ctypes.byref(n)))
         return n.value
 
-    def set_fusion(self, enable=True):
-        """Fused gather-scatter inside the RK sweeps (sem_set_fusion; on by default)."""
-        L.check(L.lib().sem_set_fusion(self._h, 1 if enable else 0))
-
     def set_adaptive(self, atol=0.0, rtol=0.0):
         """Adaptive steps for scheme "bs3" (sem_set_adaptive); dt * nsteps is then the horizon."""
         L.check(L.lib().sem_set_adaptive(self._h, float(atol), float(rtol)))

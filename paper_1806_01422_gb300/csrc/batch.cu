@@ -48,7 +48,7 @@ __device__ __forceinline__ void batch_item2(int op, const BatchDev& b, const Bat
                                             const double* u, const double* wv, double* lvec,
                                             unsigned char* smem) {
     const OpMats<double, NP>& M = *reinterpret_cast<const OpMats<double, NP>*>(b.mats + in.mats_off);
-    ElemArgs a{};   // no pending assembly (pa.input == 0)
+    ElemArgs a;
     a.u = u + in.off;
     a.w = wv ? wv + in.off : nullptr;
     a.lvec = lvec + in.loff;

@@ -88,7 +88,7 @@ extern "C" int sem_rhs_noalloc(sem_t h, const double* u, double* f, void* stream
     int rc = scratch_for_current_device(&scratch);
     if (rc != SEM_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    semk::ElemArgs a{};   // no pending assembly (pa.input == 0)
+    semk::ElemArgs a;
     a.u = u;
     a.w = nullptr;
     a.lvec = scratch;

@@ -86,101 +86,13 @@ __device__ __forceinline__ T tile_value(const ElemArgs& a, const void* g, size_t
     }
 }
 
-// Pending assembly (FP64 and double-float forms): the input node (global gx, gy,
-// gz of component c) takes out[0] of the previous apply's epilogue, formed here
-// from the previous element-local values exactly as the assembly kernel forms
-// it (same contributions, same order, same epilogue arithmetic), so the result
-// is the same bits.  A node belongs to the element holding it at local indices
-// < N on every axis; that element also writes every output of the epilogue.
-// Along one axis: local index l of element e is node (e0, l0) with e0 = e + 1,
-// l0 = 0 when l == N, else (e, l).
-template <int D>
-__device__ __forceinline__ double pend_value(const ElemArgs& a, int c, int ex, int ix, int ey, int iy, int ez, int iz,
-                                             bool write) {
-    const PendAsm& p = a.pa;
-    const int N = a.N, E = a.E, NP = N + 1;
-    auto own = [&](int e, int l, int& e0, int& l0, int& e1) {
-        e0 = l == N ? (e + 1 == E ? 0 : e + 1) : e;
-        l0 = l == N ? 0 : l;
-        e1 = e0 == 0 ? E - 1 : e0 - 1;
-        return l0 == 0;
-    };
-    int ex0, ix0, ex1, ey0 = 0, iy0 = 0, ey1 = 0, ez0 = 0, iz0 = 0, ez1 = 0;
-    const bool shx = own(ex, ix, ex0, ix0, ex1);
-    const bool shy = D >= 2 ? own(ey, iy, ey0, iy0, ey1) : false;
-    const bool shz = D >= 3 ? own(ez, iz, ez0, iz0, ez1) : false;
-    const int nsh = (int)shx + (int)shy + (int)shz;
-    const unsigned npd = D == 1 ? NP : (D == 2 ? NP * NP : NP * NP * NP);
-    auto L = [&](int qx, int lx, int qy, int ly, int qz, int lz) -> double {
-        const unsigned el = ((unsigned)qz * E + qy) * E + qx;
-        const unsigned node = ((unsigned)lz * NP + ly) * NP + lx;
-        return p.lvec[((size_t)el * D + c) * npd + node];
-    };
-    double sum = L(ex0, ix0, ey0, iy0, ez0, iz0);
-    if (shx) sum += L(ex1, N, ey0, iy0, ez0, iz0);
-    if (D >= 2 && shy) {
-        double t = L(ex0, ix0, ey1, N, ez0, iz0);
-        if (shx) t += L(ex1, N, ey1, N, ez0, iz0);
-        sum += t;
-    }
-    if (D >= 3 && shz) {
-        double t = L(ex0, ix0, ey0, iy0, ez1, N);
-        if (shx) t += L(ex1, N, ey0, iy0, ez1, N);
-        if (shy) {
-            double t2 = L(ex0, ix0, ey1, N, ez1, N);
-            if (shx) t2 += L(ex1, N, ey1, N, ez1, N);
-            t += t2;
-        }
-        sum += t;
-    }
-    const unsigned g = (unsigned)(ez0 * N + iz0) * a.G * a.G + (unsigned)(ey0 * N + iy0) * a.G + (ex0 * N + ix0);
-    const unsigned idx = c * p.GD + g;
-    double sv[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m)
-        if (m < p.nsrc) sv[m] = p.src[m][idx];
-    const bool own_node = write && ix < N && (D < 2 || iy < N) && (D < 3 || iz < N);
-    double v0 = 0.0;
-    bool bad = false;
-#pragma unroll
-    for (int o = 0; o < 3; ++o) {
-        if (o >= p.nout || (o > 0 && !own_node)) break;
-        double v = p.alpha_k[o][nsh] * sum;
-#pragma unroll
-        for (int m = 0; m < 4; ++m)
-            if (m < p.nsrc) v = fma(p.beta[o][m], sv[m], v);
-        if (o == 0) v0 = v;
-        if (own_node) {
-            p.out[o][idx] = v;
-            bad |= (__double2hiint(v) & 0x7ff00000) == 0x7ff00000;
-        }
-    }
-    if (bad && p.nonfinite) atomicOr(p.nonfinite, 1u);
-    return v0;
-}
-
-// The pending value as a tile entry of type T (times 1/k for Z = v / k).
-template <typename T, int D>
-__device__ __forceinline__ T pend_tile(const ElemArgs& a, int c, int ex, int ix, int ey, int iy, int ez, int iz,
-                                       bool write, bool scale_mult, int nb) {
-    double v = pend_value<D>(a, c, ex, ix, ey, iy, ez, iz, write);
-    if (scale_mult) v *= inv_mult<double>(nb);
-    if constexpr (std::is_same<T, dfloat>::value) {
-        float h, l;
-        split_bits(v, h, l);
-        return dfloat(h, l);
-    } else {
-        return (T)v;
-    }
-}
-
 // Load component c of a global field into an element tile (d = 3): thread t of
 // the element owns column (i, j) = (t % n, t / n) and walks k.  `scale_mult`
 // multiplies each node by 1/k (k = elements sharing it), used for Z = v / k.
 // Returns the reference value of the tile (0 unless FP32 and not Z).
 template <typename T, int NP>
 __device__ __forceinline__ T load3(T* tile, const void* g, int c, int ex, int ey, int ez, int t, bool valid,
-                                   const ElemArgs& a, bool scale_mult, int input = 0) {
+                                   const ElemArgs& a, bool scale_mult) {
     using Tl = Tile<NP>;
     const int i = t % NP, j = t / NP;
     const int N = a.N, G = a.G;
@@ -188,15 +100,6 @@ __device__ __forceinline__ T load3(T* tile, const void* g, int c, int ex, int ey
     const int nbij = (int)(i == 0 || i == N) + (int)(j == 0 || j == N);
     float ref_hi = 0.f, ref_lo = 0.f;
     if (RefSub<T>::on && !scale_mult && valid) read_pair(a, g, gidx3(c, ez * N, ey * N, ex * N, G), ref_hi, ref_lo);
-    if constexpr (!RefSub<T>::on) {
-        if (input != 0 && a.pa.input == input) {
-            for (int k = 0; k < NP; ++k)
-                tile[(k * NP + j) * Tl::P + i] =
-                    valid ? pend_tile<T, 3>(a, c, ex, i, ey, j, ez, k, true, scale_mult, nbij + (int)(k == 0 || k == N))
-                          : (T)0;
-            return (T)ref_hi;
-        }
-    }
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
         const int gz = wrap(ez * N + k, G);
@@ -211,7 +114,7 @@ __device__ __forceinline__ T load3(T* tile, const void* g, int c, int ex, int ey
 // d = 2: thread t owns row j = t and walks i.
 template <typename T, int NP>
 __device__ __forceinline__ T load2(T* tile, const void* g, int c, int ex, int ey, int t, bool valid,
-                                   const ElemArgs& a, bool scale_mult, int input = 0) {
+                                   const ElemArgs& a, bool scale_mult) {
     using Tl = Tile<NP>;
     const int j = t;
     const int N = a.N, G = a.G;
@@ -220,15 +123,6 @@ __device__ __forceinline__ T load2(T* tile, const void* g, int c, int ex, int ey
     const size_t row = ((size_t)c * G + gy) * G;
     float ref_hi = 0.f, ref_lo = 0.f;
     if (RefSub<T>::on && !scale_mult && valid) read_pair(a, g, ((size_t)c * G + ey * N) * G + ex * N, ref_hi, ref_lo);
-    if constexpr (!RefSub<T>::on) {
-        if (input != 0 && a.pa.input == input) {
-            for (int i = 0; i < NP; ++i)
-                tile[j * Tl::P + i] =
-                    valid ? pend_tile<T, 2>(a, c, ex, i, ey, j, 0, 0, true, scale_mult, nbj + (int)(i == 0 || i == N))
-                          : (T)0;
-            return (T)ref_hi;
-        }
-    }
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
         const int gx = wrap(ex * N + i, G);
@@ -408,7 +302,7 @@ __global__ void rhs3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
     const int ex = e % a.E, ey = (e / a.E) % a.E, ez = e / (a.E * a.E);
     T rU[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) rU[c] = load3<T, NP>(sU[c], a.u, c, ex, ey, ez, t, valid, a, false, 1);
+    for (int c = 0; c < 3; ++c) rU[c] = load3<T, NP>(sU[c], a.u, c, ex, ey, ez, t, valid, a, false);
     __syncthreads();
     if constexpr (shared_pass3<T, NP>()) {
         df3_body<T, NP>(M, a, OP_RHS, sU, sU, sF, sA, rU, rU, e, t, valid);
@@ -450,8 +344,8 @@ __global__ void jac3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
     T rU[3], rW[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        rU[c] = load3<T, NP>(sU[c], a.u, c, ex, ey, ez, t, valid, a, false, 1);
-        rW[c] = load3<T, NP>(sW[c], a.w, c, ex, ey, ez, t, valid, a, false, 2);
+        rU[c] = load3<T, NP>(sU[c], a.u, c, ex, ey, ez, t, valid, a, false);
+        rW[c] = load3<T, NP>(sW[c], a.w, c, ex, ey, ez, t, valid, a, false);
     }
     __syncthreads();
     if constexpr (shared_pass3<T, NP>()) {
@@ -494,8 +388,8 @@ __global__ void jact3_kernel(const __grid_constant__ OpMats<T, NP> M, const Elem
     T rU[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        rU[c] = load3<T, NP>(sU[c], a.u, c, ex, ey, ez, t, valid, a, false, 1);
-        load3<T, NP>(sZ[c], a.w, c, ex, ey, ez, t, valid, a, true, 2);
+        rU[c] = load3<T, NP>(sU[c], a.u, c, ex, ey, ez, t, valid, a, false);
+        load3<T, NP>(sZ[c], a.w, c, ex, ey, ez, t, valid, a, true);
     }
     __syncthreads();
     if constexpr (shared_pass3<T, NP>()) {
@@ -537,7 +431,7 @@ __device__ __forceinline__ void rhs2_body(const OpMats<T, NP>& M, const ElemArgs
     const int ex = e % a.E, ey = e / a.E;
     T rU[2];
 #pragma unroll
-    for (int c = 0; c < 2; ++c) rU[c] = load2<T, NP>(sU[c], a.u, c, ex, ey, t, valid, a, false, 1);
+    for (int c = 0; c < 2; ++c) rU[c] = load2<T, NP>(sU[c], a.u, c, ex, ey, t, valid, a, false);
     __syncthreads();
     const int xb = t * P, yb = t;
     auto* out = reinterpret_cast<typename OutT<T>::type*>(a.lvec) + (size_t)e * 2 * (NP * NP) + t;
@@ -578,8 +472,8 @@ __device__ __forceinline__ void jac2_body(const OpMats<T, NP>& M, const ElemArgs
     T rU[2], rW[2];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-        rU[c] = load2<T, NP>(sU[c], a.u, c, ex, ey, t, valid, a, false, 1);
-        rW[c] = load2<T, NP>(sW[c], a.w, c, ex, ey, t, valid, a, false, 2);
+        rU[c] = load2<T, NP>(sU[c], a.u, c, ex, ey, t, valid, a, false);
+        rW[c] = load2<T, NP>(sW[c], a.w, c, ex, ey, t, valid, a, false);
     }
     __syncthreads();
     const int xb = t * P, yb = t;
@@ -621,8 +515,8 @@ __device__ __forceinline__ void jact2_body(const OpMats<T, NP>& M, const ElemArg
     T rU[2];
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-        rU[c] = load2<T, NP>(sU[c], a.u, c, ex, ey, t, valid, a, false, 1);
-        load2<T, NP>(sZ[c], a.w, c, ex, ey, t, valid, a, true, 2);
+        rU[c] = load2<T, NP>(sU[c], a.u, c, ex, ey, t, valid, a, false);
+        load2<T, NP>(sZ[c], a.w, c, ex, ey, t, valid, a, true);
     }
     __syncthreads();
     const int xb = t * P, yb = t;
@@ -667,7 +561,7 @@ __device__ __forceinline__ void rhs2c_body(const OpMats<T, NP>& M, const ElemArg
     T* sU[2] = {sm, sm + S2};
     T* sF = sm + (2 + c) * S2;
     const int ex = e % a.E, ey = e / a.E;
-    const T ru0 = load2<T, NP>(sU[c], a.u, c, ex, ey, t, valid, a, false, 1);
+    const T ru0 = load2<T, NP>(sU[c], a.u, c, ex, ey, t, valid, a, false);
     (void)ru0;
     __syncthreads();
     const T rU[2] = {(T)0, (T)0};   // no reference subtraction in this form
@@ -695,8 +589,8 @@ __device__ __forceinline__ void jac2c_body(const OpMats<T, NP>& M, const ElemArg
     T* sW[2] = {sm + 2 * S2, sm + 3 * S2};
     T* sF = sm + (4 + c) * S2;
     const int ex = e % a.E, ey = e / a.E;
-    load2<T, NP>(sU[c], a.u, c, ex, ey, t, valid, a, false, 1);
-    load2<T, NP>(sW[c], a.w, c, ex, ey, t, valid, a, false, 2);
+    load2<T, NP>(sU[c], a.u, c, ex, ey, t, valid, a, false);
+    load2<T, NP>(sW[c], a.w, c, ex, ey, t, valid, a, false);
     __syncthreads();
     const T rz = (T)0;
     const int xb = t * P, yb = t;
@@ -752,8 +646,8 @@ __device__ __forceinline__ void jact2c_body(const OpMats<T, NP>& M, const ElemAr
     T* sZ[2] = {sm + 2 * S2, sm + 3 * S2};
     T* sF = sm + (4 + l) * S2;
     const int ex = e % a.E, ey = e / a.E;
-    load2<T, NP>(sU[l], a.u, l, ex, ey, t, valid, a, false, 1);
-    load2<T, NP>(sZ[l], a.w, l, ex, ey, t, valid, a, true, 2);
+    load2<T, NP>(sU[l], a.u, l, ex, ey, t, valid, a, false);
+    load2<T, NP>(sZ[l], a.w, l, ex, ey, t, valid, a, true);
     __syncthreads();
     const T rU[2] = {(T)0, (T)0};
     const int xb = t * P, yb = t;

@@ -175,21 +175,6 @@ inline dfloat to_coeff<dfloat>(double x) {
     return dfloat_of(x);
 }
 
-// The gather-scatter sum and epilogue of the previous operator apply, run by the
-// next element kernel while it loads its input (FP64 sums; see pend_value in
-// op_elem.cuh).  out[0] is that input.
-struct PendAsm {
-    const double* lvec;     // element-local values of the previous apply
-    double* out[3];
-    const double* src[4];
-    double alpha_k[3][4];   // alpha of output o with the 1/2^k multiplicity folded in (k sharing axes)
-    double beta[3][4];
-    unsigned* nonfinite;
-    int nout, nsrc;
-    int input;              // 0: none, 1: out[0] is the input u, 2: out[0] is the input w
-    unsigned GD;            // G^d, the component stride of a state
-};
-
 // Launch-time arguments shared by the element kernels.
 struct ElemArgs {
     const void* u;     // state at which the operator is evaluated (global, SoA)
@@ -199,7 +184,6 @@ struct ElemArgs {
     int nelem;         // E^d
     unsigned plane;    // unknowns per vector: offset of the lo plane of a float-pair input
     int in_f2;         // FP32 form: inputs are float-pair planes (1) or doubles (0)
-    PendAsm pa;        // pending assembly of the previous apply (pa.input == 0: none)
 };
 
 // Global index of component c at unique node (gz, gy, gx) of a d-dimensional grid.

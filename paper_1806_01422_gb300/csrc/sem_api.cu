@@ -143,15 +143,7 @@ struct sem_ctx {
     unsigned* flag = nullptr;    // non-finite flag
     double* vecs = nullptr;      // NVEC state-sized work vectors
     double* frozen = nullptr;    // frozen advecting field a (a state; float pairs in the FP32 form) or null
-    // fused gather-scatter: an apply may leave its assembly pending, to be run by the
-    // next element kernel while it loads the assembled input (FP64 and FP64-DF)
-    bool fuse = false;
-    double* lvec2 = nullptr;     // second element-local buffer (the pending one is read while the next is written)
-    bool pend = false;
     long long nlaunch = 0;       // element and assembly launches since the last forward sweep began
-    Epi pend_ep;
-    void* pend_lvec = nullptr;
-    int pend_scale = 0;
     double* traj = nullptr;
     size_t traj_vectors = 0;
     // last forward sweep
@@ -282,14 +274,6 @@ int ensure_workspace(sem_t h) {
         return fail(e == cudaErrorMemoryAllocation ? SEM_ERR_OOM : SEM_ERR_CUDA, "workspace allocation: %s",
                     cudaGetErrorString(e));
     }
-    if (!h->batch && !f32(h) && h->dim >= 2) {   // second element-local buffer of the fused assembly
-        cudaError_t e2 = cudaMalloc(&h->lvec2, h->lvec_elems * sizeof(double));
-        if (e2 != cudaSuccess) {
-            cudaGetLastError();
-            h->lvec2 = nullptr;
-            h->fuse = false;   // run every assembly on its own instead
-        }
-    }
     return SEM_OK;
 }
 
@@ -387,40 +371,8 @@ AsmArgs asm_args(sem_t h, int scale_mult) {
     return aa;
 }
 
-// Run the pending assembly as its own launch (when the next consumer cannot take it over).
-int flush_pending(sem_t h, cudaStream_t s) {
-    if (!h->pend) return SEM_OK;
-    h->pend = false;
-    long long slot;
-    SEM_TRY(prof_begin(h, 3, s, slot));
-    cudaError_t e = launch_assemble(false, h->pend_lvec, asm_args(h, h->pend_scale), h->pend_ep, s);
-    if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "assembly launch: %s", cudaGetErrorString(e));
-    SEM_TRY(prof_end(h, slot, s));
-    ++h->nlaunch;
-    return SEM_OK;
-}
-
-bool is_output(const Epi& ep, const void* p) {
-    for (int o = 0; o < ep.nout; ++o)
-        if (ep.out[o] == p) return true;
-    return false;
-}
-
-// The assembly of this apply may be deferred into the next element kernel: FP64 or
-// FP64-DF, a single instance, the plain kernels (not the lean 3D ones), and no
-// source of out[0] (the next kernel's input) among the outputs written in place.
-bool can_defer(sem_t h, const Epi& ep) {
-    if (!h->fuse || !h->lvec2 || h->batch || f32(h) || h->dim == 1 || (h->dim == 3 && h->np >= 13)) return false;
-    for (int m = 0; m < ep.nsrc; ++m)
-        if (ep.beta[0][m] != 0.0 && is_output(ep, ep.src[m])) return false;
-    return true;
-}
-
-// One operator apply: element kernel (which also finishes a pending assembly whose out[0]
-// is one of its inputs), then the gather-scatter with the epilogue `ep`, or, with defer,
-// that gather-scatter left pending for the next apply.
-int apply(sem_t h, int op, const double* u, const double* w, const Epi& ep, cudaStream_t s, bool f2_in = false,
-          bool defer = false) {
+// One operator apply: element kernel, then the gather-scatter with the epilogue `ep`.
+int apply(sem_t h, int op, const double* u, const double* w, const Epi& ep, cudaStream_t s, bool f2_in = false) {
     if (h->batch) return batch_apply(h, op, u, w, ep, s);
     ElemArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -433,35 +385,6 @@ int apply(sem_t h, int op, const double* u, const double* w, const Epi& ep, cuda
     a.N = h->N;
     a.G = h->G;
     a.nelem = h->nelem;
-    if (h->pend) {
-        const void* in = h->pend_ep.out[0];
-        int input = 0;
-        if (u == in && (op == OP_RHS || !is_output(h->pend_ep, w))) input = 1;
-        else if (op != OP_RHS && w == in && !is_output(h->pend_ep, u)) input = 2;
-        if (input == 0) {
-            SEM_TRY(flush_pending(h, s));
-        } else {
-            PendAsm& p = a.pa;
-            const Epi& pe = h->pend_ep;
-            p.lvec = (const double*)h->pend_lvec;
-            for (int o = 0; o < 3; ++o) {
-                p.out[o] = pe.out[o];
-                for (int k = 0; k < 4; ++k) p.alpha_k[o][k] = h->pend_scale ? pe.alpha[o] / (double)(1 << k) : pe.alpha[o];
-                for (int m = 0; m < 4; ++m) p.beta[o][m] = pe.beta[o][m];
-            }
-            for (int m = 0; m < 4; ++m) p.src[m] = pe.src[m];
-            p.nout = pe.nout;
-            p.nsrc = pe.nsrc;
-            p.nonfinite = pe.nonfinite;
-            p.input = input;
-            p.GD = (unsigned)(h->ndof / h->dim);
-            // the element results go to the other buffer while the pending ones are read
-            // (allocated with the workspace: no allocation may happen while a graph records)
-            if (!h->lvec2) return fail(SEM_ERR_STATE, "fused assembly without its second buffer");
-            a.lvec = h->pend_lvec == h->lvec ? (void*)h->lvec2 : h->lvec;
-            h->pend = false;
-        }
-    }
     const bool f32 = h->precision == SEM_PREC_FP32_BULK;
     long long slot;
     SEM_TRY(prof_begin(h, op, s, slot));
@@ -481,13 +404,6 @@ int apply(sem_t h, int op, const double* u, const double* w, const Epi& ep, cuda
     if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "element kernel launch: %s", cudaGetErrorString(e));
     SEM_TRY(prof_end(h, slot, s));
     ++h->nlaunch;
-    if (defer && can_defer(h, ep)) {
-        h->pend = true;
-        h->pend_ep = ep;
-        h->pend_lvec = a.lvec;
-        h->pend_scale = op != OP_JACT;
-        return SEM_OK;
-    }
     SEM_TRY(prof_begin(h, 3, s, slot));
     e = launch_assemble(f32, a.lvec, asm_args(h, op != OP_JACT), ep, s);
     if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "assembly launch: %s", cudaGetErrorString(e));
@@ -519,9 +435,9 @@ int add_src(Epi& ep, const double* p) {
 // non-null the last stage writes u_{n+1} = un + dt sum_i b_i k_i; otherwise the
 // step stops after Y_s (taping only: s-1 applies).
 // The stage derivative k = F(Y), or J(a) Y with a frozen advecting field a.
-int stage_rhs(sem_t h, const double* Y, const Epi& ep, cudaStream_t s, bool defer = false) {
-    if (h->frozen) return apply(h, OP_JAC, h->frozen, Y, ep, s, f32(h), defer);
-    return apply(h, OP_RHS, Y, nullptr, ep, s, f32(h), defer);
+int stage_rhs(sem_t h, const double* Y, const Epi& ep, cudaStream_t s) {
+    if (h->frozen) return apply(h, OP_JAC, h->frozen, Y, ep, s, f32(h));
+    return apply(h, OP_RHS, Y, nullptr, ep, s, f32(h));
 }
 
 // The linearisation point of the adjoint stage: Y itself, or the frozen field.
@@ -559,7 +475,7 @@ int rk_stages(sem_t h, const Tableau& T, double dt, const double* un, double* co
                 ep.beta[0][sa] = 1.0;
                 ep.nout = 1;
             }
-            SEM_TRY(stage_rhs(h, i == 0 ? un : Y[i], ep, s, i < last));
+            SEM_TRY(stage_rhs(h, i == 0 ? un : Y[i], ep, s));
             ++count;
         }
         return SEM_OK;
@@ -588,7 +504,7 @@ int rk_stages(sem_t h, const Tableau& T, double dt, const double* un, double* co
                 if (T.b[j] != 0.0) ep.beta[0][add_src(ep, vec(h, V_K0 + j))] = dt * T.b[j];
             ep.nout = 1;
         }
-        SEM_TRY(stage_rhs(h, Yi, ep, s, i < last));
+        SEM_TRY(stage_rhs(h, Yi, ep, s));
         ++count;
     }
     return SEM_OK;
@@ -635,7 +551,7 @@ int rk_adjoint_step(sem_t h, const Tableau& T, double dt, const double* const* Y
                 ep.beta[1][sa] = c;
                 ep.nout = 2;
             }
-            SEM_TRY(apply(h, OP_JACT, jac_point(h, Y[i]), nu, ep, s, f32(h), i > 0));
+            SEM_TRY(apply(h, OP_JACT, jac_point(h, Y[i]), nu, ep, s, f32(h)));
             ++count;
         }
         return SEM_OK;
@@ -666,7 +582,7 @@ int rk_adjoint_step(sem_t h, const Tableau& T, double dt, const double* const* Y
             for (int m = 0; m < ep.nsrc; ++m) ep.beta[1][m] = c * ep.beta[0][m];
             ep.nout = 2;
         }
-        SEM_TRY(apply(h, OP_JACT, jac_point(h, Y[i]), nu, ep, s, f32(h), i > 0));
+        SEM_TRY(apply(h, OP_JACT, jac_point(h, Y[i]), nu, ep, s, f32(h)));
         ++count;
     }
     return SEM_OK;
@@ -1674,7 +1590,6 @@ void sem_destroy(sem_t h) {
     cudaFree(h->kpart);
     cudaFree(h->kscal);
     cudaFree(h->frozen);
-    cudaFree(h->lvec2);
     cudaFree(h->adapt_buf);
     if (h->host_traj) cudaFreeHost(h->host_traj);
     for (int k = 0; k < 3; ++k) {
@@ -1950,18 +1865,6 @@ int sem_set_advection(sem_t h, const double* a, void* stream) {
 int sem_launch_count(sem_t h, long long* launches) {
     if (!h || !launches) return fail(SEM_ERR_ARG, "null handle or output");
     *launches = h->nlaunch;
-    return SEM_OK;
-}
-
-int sem_set_fusion(sem_t h, int enable) {
-    if (!h) return fail(SEM_ERR_ARG, "null handle");
-    h->fuse = enable != 0;
-    if (h->graph_exec) {   // a recorded gradient graph follows the old launch sequence
-        cudaGraphExecDestroy(h->graph_exec);
-        h->graph_exec = nullptr;
-        h->graph_key = sem_ctx::GraphKey{-1, 0, 0.0, nullptr, nullptr, nullptr};
-        prof_graph_release(h);
-    }
     return SEM_OK;
 }
 

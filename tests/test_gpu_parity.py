@@ -320,31 +320,3 @@ def test_inviscid_and_zero_fields(prec):
     z = np.zeros_like(u)
     assert float(s.rhs(z).abs().max()) == 0.0          # F(0) = 0 exactly
     assert float(s.jacT(z, z).abs().max()) == 0.0
-
-
-# Fused gather-scatter inside the sweeps: the same bits as separate assembly launches.
-@pytest.mark.parametrize("dim,E,N,scheme,ckpt,prec", [(2, 6, 7, "ssprk3", "stages", "fp64"),
-                                                      (2, 5, 4, "rk4", "states", "fp64"),
-                                                      (3, 3, 5, "rk4", "binomial", "fp64"),
-                                                      (2, 6, 7, "ssprk3", "stages", "fp64_df"),
-                                                      (3, 2, 7, "ssprk3", "states", "fp64_df"),
-                                                      (2, 4, 3, "euler", "stages", "fp64")])
-def test_fused_assembly_is_bitwise_equal_to_separate_launches(dim, E, N, scheme, ckpt, prec):
-    s = Sem(dim, E, N, 1e-3 if dim == 2 else 5e-4, precision=prec, ckpt=ckpt, ckpt_slots=3)
-    x = s.coords()
-    u0, uo = inputs.workload_field(dim, x, 1), inputs.workload_field(dim, x, 2)
-    s.set_fusion(True)
-    J1, g1 = s.objective_grad(u0, uo, 2e-4, 12, scheme)
-    n_fused = s.launch_count()
-    g1 = g1.clone()
-    uT1 = s.rk_forward(u0, 2e-4, 12, scheme).clone()
-    s.set_fusion(False)
-    J0, g0 = s.objective_grad(u0, uo, 2e-4, 12, scheme)
-    n_plain = s.launch_count()
-    uT0 = s.rk_forward(u0, 2e-4, 12, scheme)
-    assert J1 == J0 and torch.equal(g1, g0) and torch.equal(uT1, uT0)
-    assert n_fused < n_plain            # the deferred assemblies were not launched
-    s.set_fusion(True)
-    s.use_graph(True)
-    J2, g2 = s.objective_grad(u0, uo, 2e-4, 12, scheme)
-    assert J2 == J0 and torch.equal(g2, g0)
