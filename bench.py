@@ -10,7 +10,7 @@ with the matrix-free transpose Jacobian, all on one GPU through the C ABI.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 N > 1 runs one independent replica per GPU (torchrun, one rank per GPU): the
-path has no exchange step on one box, so scaling is weak.  Prints one JSON line.
+path has no exchange step between GPUs, so scaling is weak.  Prints one JSON line.
 """
 import argparse
 import hashlib
@@ -621,7 +621,7 @@ def main():
     ap.add_argument("--order-sweep", action="store_true",
                     help="standalone 3D F and J^T throughput over N in {3,5,7,9,11,15} at ~34M unknowns")
     ap.add_argument("--ops-once", nargs=4, metavar=("DIM", "E", "N", "PRECISION"),
-                    help="profiling driver: one F and one J^T apply on the workload field of that size, no timing")
+                    help="for ncu: one F and one J^T apply on the workload field of that size, no timing")
     args = ap.parse_args()
 
     if args.oracle_sample:

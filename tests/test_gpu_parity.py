@@ -1,7 +1,7 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
-Tolerances: FP64 form 1e-11 relative (max-norm over the output array, the
-spec bound); FP32-bulk form 1e-5 relative on smooth workload fields;
+Tolerances: FP64 form 1e-11 relative (max-norm over the output array); FP32-bulk
+form 1e-5 relative on smooth workload fields;
 gather-scatter results are bitwise reproducible run to run.
 """
 import numpy as np
