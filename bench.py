@@ -614,7 +614,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--lbfgs", type=int, default=0, metavar="K",
                     help="after the timed region, run K L-BFGS iterations recovering u0 (single-instance workloads)")
-    ap.add_argument("--profile-every", type=int, default=16, help="time one launch in this many per kernel kind")
+    ap.add_argument("--profile-every", type=int, default=64, help="time one launch in this many per kernel kind")
     ap.add_argument("--no-graph", action="store_true", help="launch on the stream instead of replaying a CUDA graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-sample", nargs=2, metavar=("WORKLOAD", "RK_STEPS"), help=argparse.SUPPRESS)

@@ -194,6 +194,16 @@ int sem_sweep_stats(sem_t h, long long* out3);
  * forward sweep and any recorded gradient graph. */
 int sem_set_advection(sem_t h, const double* a, void* stream);
 
+/* Programmatic dependent launch (process-wide; on by default; no counterpart in
+ * the paper).  Element and assembly kernels are launched with the programmatic
+ * stream-serialization attribute: the next kernel's blocks may be scheduled
+ * while the previous one finishes, each kernel waiting for its predecessor's
+ * completion and memory before it reads anything, so only launch latency is
+ * hidden and results are unchanged.  enable = 0 launches them the ordinary way
+ * (for comparison).  Affects launches made after the call, and graphs recorded
+ * after it. */
+int sem_set_dependent_launch(int enable);
+
 /* Element-kernel and assembly launches made by operator applies since the last
  * forward sweep began (its adjoint sweep included; a recorded gradient graph
  * replays the launches counted while it was recorded).  Host-only. */

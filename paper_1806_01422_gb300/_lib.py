@@ -59,6 +59,7 @@ _SIGS = {
     "sem_set_host_tier": (_I, [_H, ctypes.c_size_t]),
     "sem_set_adaptive": (_I, [_H, _D, _D]),
     "sem_launch_count": (_I, [_H, ctypes.POINTER(ctypes.c_longlong)]),
+    "sem_set_dependent_launch": (_I, [_I]),
     "sem_adaptive_steps": (_I, [_H, ctypes.POINTER(_I), ctypes.POINTER(_I), _P, _I]),
     "sem_trajectory_info": (_I, [_H, ctypes.POINTER(ctypes.c_longlong)]),
     "sem_solver_stats": (_I, [_H, ctypes.POINTER(ctypes.c_longlong)]),

@@ -292,6 +292,7 @@ __global__ void rhs3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
     using Tl = Tile<NP>;
     constexpr int TPE = NP * NP, P = Tl::P, S2 = Tl::S2, S3 = Tl::S3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_wait();
     const int el = threadIdx.x / TPE, t = threadIdx.x % TPE;
     const int e = blockIdx.x * (blockDim.x / TPE) + el;
     const bool valid = e < a.nelem;
@@ -304,6 +305,7 @@ __global__ void rhs3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
 #pragma unroll
     for (int c = 0; c < 3; ++c) rU[c] = load3<T, NP>(sU[c], a.u, c, ex, ey, ez, t, valid, a, false);
     __syncthreads();
+    pdl_trigger();
     if constexpr (shared_pass3<T, NP>()) {
         df3_body<T, NP>(M, a, OP_RHS, sU, sU, sF, sA, rU, rU, e, t, valid);
         return;
@@ -332,6 +334,7 @@ __global__ void jac3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
     using Tl = Tile<NP>;
     constexpr int TPE = NP * NP, P = Tl::P, S2 = Tl::S2, S3 = Tl::S3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_wait();
     const int el = threadIdx.x / TPE, t = threadIdx.x % TPE;
     const int e = blockIdx.x * (blockDim.x / TPE) + el;
     const bool valid = e < a.nelem;
@@ -348,6 +351,7 @@ __global__ void jac3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
         rW[c] = load3<T, NP>(sW[c], a.w, c, ex, ey, ez, t, valid, a, false);
     }
     __syncthreads();
+    pdl_trigger();
     if constexpr (shared_pass3<T, NP>()) {
         df3_body<T, NP>(M, a, OP_JAC, sU, sW, sF, sA, rU, rW, e, t, valid);
         return;
@@ -376,6 +380,7 @@ __global__ void jact3_kernel(const __grid_constant__ OpMats<T, NP> M, const Elem
     using Tl = Tile<NP>;
     constexpr int TPE = NP * NP, P = Tl::P, S2 = Tl::S2, S3 = Tl::S3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_wait();
     const int el = threadIdx.x / TPE, t = threadIdx.x % TPE;
     const int e = blockIdx.x * (blockDim.x / TPE) + el;
     const bool valid = e < a.nelem;
@@ -392,6 +397,7 @@ __global__ void jact3_kernel(const __grid_constant__ OpMats<T, NP> M, const Elem
         load3<T, NP>(sZ[c], a.w, c, ex, ey, ez, t, valid, a, true);
     }
     __syncthreads();
+    pdl_trigger();
     if constexpr (shared_pass3<T, NP>()) {
         df3_body<T, NP>(M, a, OP_JACT, sU, sZ, sF, sA, rU, rU, e, t, valid);
         return;
@@ -453,6 +459,7 @@ __device__ __forceinline__ void rhs2_body(const OpMats<T, NP>& M, const ElemArgs
 template <typename T, int NP>
 __global__ void rhs2_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_wait();
     const int el = threadIdx.x / NP, t = threadIdx.x % NP;
     const int e = blockIdx.x * (blockDim.x / NP) + el;
     rhs2_body<T, NP>(M, a, e, t, el, e < a.nelem, smem_raw);
@@ -496,6 +503,7 @@ __device__ __forceinline__ void jac2_body(const OpMats<T, NP>& M, const ElemArgs
 template <typename T, int NP>
 __global__ void jac2_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_wait();
     const int el = threadIdx.x / NP, t = threadIdx.x % NP;
     const int e = blockIdx.x * (blockDim.x / NP) + el;
     jac2_body<T, NP>(M, a, e, t, el, e < a.nelem, smem_raw);
@@ -539,6 +547,7 @@ __device__ __forceinline__ void jact2_body(const OpMats<T, NP>& M, const ElemArg
 template <typename T, int NP>
 __global__ void jact2_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_wait();
     const int el = threadIdx.x / NP, t = threadIdx.x % NP;
     const int e = blockIdx.x * (blockDim.x / NP) + el;
     jact2_body<T, NP>(M, a, e, t, el, e < a.nelem, smem_raw);
@@ -672,6 +681,7 @@ __device__ __forceinline__ void jact2c_body(const OpMats<T, NP>& M, const ElemAr
 template <typename T, int NP>
 __global__ void __launch_bounds__(256, 2) op2c_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a, int op) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_wait();
     const int half = blockDim.x / 2;
     const int c = threadIdx.x >= half, r = threadIdx.x - c * half;
     const int el = r / NP, t = r % NP;
@@ -696,6 +706,7 @@ __device__ __forceinline__ T load1(T (&x)[NP], const void* g, int e, const ElemA
 
 template <typename T, int NP>
 __global__ void op1_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a, int op) {
+    pdl_wait();
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= a.nelem) return;
     T u[NP], f[NP];

@@ -40,6 +40,7 @@ rhs3_lean_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
     using Tl = Tile<NP>;
     constexpr int P = Tl::P, S2 = Tl::S2, S3 = Tl::S3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_wait();
     const int t = threadIdx.x;
     const int e = blockIdx.x;
     T* sm = reinterpret_cast<T*>(smem_raw);
@@ -152,6 +153,7 @@ jac3_lean_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
     using Tl = Tile<NP>;
     constexpr int P = Tl::P, S2 = Tl::S2, S3 = Tl::S3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_wait();
     const int t = threadIdx.x;
     const int e = blockIdx.x;
     T* sm = reinterpret_cast<T*>(smem_raw);
@@ -192,6 +194,7 @@ jact3_lean_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
     using Tl = Tile<NP>;
     constexpr int P = Tl::P, S2 = Tl::S2, S3 = Tl::S3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_wait();
     const int t = threadIdx.x;
     const int e = blockIdx.x;
     T* sm = reinterpret_cast<T*>(smem_raw);

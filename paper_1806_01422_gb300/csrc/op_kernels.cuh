@@ -147,6 +147,36 @@ __device__ __forceinline__ void st_line(T* s, int base, const T (&x)[NP]) {
     for (int m = 0; m < NP; ++m) s[base + m * STRIDE] = x[m];
 }
 
+// ---------------------------------------------------------------- dependent launches
+// Programmatic dependent launch (sm_90 and later): the element and assembly
+// kernels are launched with the programmatic stream-serialization attribute, so
+// a kernel's blocks may be scheduled while its predecessor in the stream is
+// still finishing.  Every such kernel first waits until its predecessors have
+// completed and their memory is visible (griddepcontrol.wait; immediate for a
+// kernel launched the ordinary way), and signals once it no longer needs to keep
+// its successor from starting (griddepcontrol.launch_dependents).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Process-wide switch of the attribute (on by default; sem_set_dependent_launch).
+bool pdl_enabled();
+
+// Launch kernel k with the programmatic stream-serialization attribute.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // Element-local output type: the compute type, except double for double-float
 // kernels (whose results go to the FP64 assembly).
 template <typename T>

@@ -54,8 +54,7 @@ cudaError_t launch_elem_np(int op, const double* mats, const ElemArgs& a, cudaSt
     if constexpr (D == 1) {
         const int threads = 128;
         const int blocks = (a.nelem + threads - 1) / threads;
-        op1_kernel<T, NP><<<blocks, threads, 0, s>>>(M, a, op);
-        return cudaGetLastError();
+        return launch_pdl(op1_kernel<T, NP>, dim3(blocks), dim3(threads), 0, s, M, a, op);
     } else {
         constexpr int TPE = D == 3 ? NP * NP : (comp_parallel<T, D>() ? 2 * NP : NP);
         constexpr bool lean = D == 3 && lean3<T, NP>();
@@ -93,8 +92,7 @@ cudaError_t launch_elem_np(int op, const double* mats, const ElemArgs& a, cudaSt
                     done_c_smem = smem;
                 }
             }
-            op2c_kernel<T, NP><<<blocks, threads, smem, s>>>(M, a, op);
-            return cudaGetLastError();
+            return launch_pdl(op2c_kernel<T, NP>, dim3(blocks), dim3(threads), smem, s, M, a, op);
         }
         void (*k)(const OpMats<T, NP>, const ElemArgs);
         if constexpr (lean)
@@ -119,8 +117,7 @@ cudaError_t launch_elem_np(int op, const double* mats, const ElemArgs& a, cudaSt
                 done_smem[op][0] = smem;
             }
         }
-        k<<<blocks, threads, smem, s>>>(M, a);
-        return cudaGetLastError();
+        return launch_pdl(k, dim3(blocks), dim3(threads), smem, s, M, a);
     }
 }
 

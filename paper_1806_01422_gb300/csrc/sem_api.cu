@@ -1862,6 +1862,11 @@ int sem_set_advection(sem_t h, const double* a, void* stream) {
     return SEM_OK;
 }
 
+int sem_set_dependent_launch(int enable) {
+    semk::set_pdl(enable != 0);
+    return SEM_OK;
+}
+
 int sem_launch_count(sem_t h, long long* launches) {
     if (!h || !launches) return fail(SEM_ERR_ARG, "null handle or output");
     *launches = h->nlaunch;

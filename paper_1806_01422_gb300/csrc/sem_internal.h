@@ -17,6 +17,7 @@ cudaError_t launch_elem(int np, int op, const double* mats, const ElemArgs& a, c
 
 // Largest supported point count per (D, T): limited by the shared-memory tiles.
 int max_np(int D, bool fp32);
+void set_pdl(bool on);   // programmatic dependent launch of element and assembly kernels
 
 // --------------------------------------------------------------- assembly
 // Epilogue of the gather-scatter sum: for each unique scalar node with

@@ -10,6 +10,7 @@
 // per axis), so the result is bitwise reproducible run to run.
 #include <math.h>
 
+#include <atomic>
 #include <type_traits>
 
 #include "df64.cuh"
@@ -47,6 +48,7 @@ __device__ __forceinline__ A pick4(const A (&t)[4], int k) {
 template <typename T, int D, int NOUT, int NSRC>
 __global__ void __launch_bounds__(128) assemble_kernel(const T* __restrict__ lvec, const AsmArgs a,
                                                        const Epi ep) {
+    pdl_wait();
     const int gx = blockIdx.x * blockDim.x + threadIdx.x;
     if (gx >= a.G) return;
     int gy = 0, gz = 0, c = 0;
@@ -133,6 +135,7 @@ struct EpiF2 {
 template <int D, int NOUT, int NSRC, bool F2>
 __global__ void __launch_bounds__(128) assemble_f32_kernel(const float* __restrict__ lvec, const AsmArgs a,
                                                            const EpiF2 ep) {
+    pdl_wait();
     const int gx = blockIdx.x * blockDim.x + threadIdx.x;
     if (gx >= a.G) return;
     int gy = 0, gz = 0, c = 0;
@@ -207,6 +210,10 @@ __global__ void __launch_bounds__(128) assemble_f32_kernel(const float* __restri
     }
 }
 
+static std::atomic<bool> g_pdl{true};
+bool pdl_enabled() { return g_pdl.load(std::memory_order_relaxed); }
+void set_pdl(bool on) { g_pdl.store(on, std::memory_order_relaxed); }
+
 static df df_of(double x) {
     df r;
     r.hi = (float)x;
@@ -253,13 +260,14 @@ cudaError_t launch_assemble(bool lvec_fp32, const void* lvec, const AsmArgs& a_i
         grid.z = 3 * a.G;
     }
     if (ep.nout < 1 || ep.nout > 3 || ep.nsrc < 0 || ep.nsrc > 4) return cudaErrorInvalidValue;
+    cudaError_t err = cudaSuccess;
 #define SEMK_ASM_NS(T, D, NO)                                                                          \
     switch (ep.nsrc) {                                                                                 \
-        case 0: assemble_kernel<T, D, NO, 0><<<grid, threads, 0, s>>>((const T*)lvec, a, ep); break; \
-        case 1: assemble_kernel<T, D, NO, 1><<<grid, threads, 0, s>>>((const T*)lvec, a, ep); break; \
-        case 2: assemble_kernel<T, D, NO, 2><<<grid, threads, 0, s>>>((const T*)lvec, a, ep); break; \
-        case 3: assemble_kernel<T, D, NO, 3><<<grid, threads, 0, s>>>((const T*)lvec, a, ep); break; \
-        default: assemble_kernel<T, D, NO, 4><<<grid, threads, 0, s>>>((const T*)lvec, a, ep); break; \
+        case 0: err = launch_pdl(assemble_kernel<T, D, NO, 0>, grid, dim3(threads), 0, s, (const T*)lvec, a, ep); break; \
+        case 1: err = launch_pdl(assemble_kernel<T, D, NO, 1>, grid, dim3(threads), 0, s, (const T*)lvec, a, ep); break; \
+        case 2: err = launch_pdl(assemble_kernel<T, D, NO, 2>, grid, dim3(threads), 0, s, (const T*)lvec, a, ep); break; \
+        case 3: err = launch_pdl(assemble_kernel<T, D, NO, 3>, grid, dim3(threads), 0, s, (const T*)lvec, a, ep); break; \
+        default: err = launch_pdl(assemble_kernel<T, D, NO, 4>, grid, dim3(threads), 0, s, (const T*)lvec, a, ep); break; \
     }
 #define SEMK_ASM_NO(T, D)                           \
     switch (ep.nout) {                              \
@@ -274,10 +282,9 @@ cudaError_t launch_assemble(bool lvec_fp32, const void* lvec, const AsmArgs& a_i
             EpiF2 e2{};
             e2.out_f64 = ep.out[0];
             e2.nonfinite = ep.nonfinite;
-            if (a.D == 1) assemble_f32_kernel<1, 1, 0, false><<<grid, threads, 0, s>>>((const float*)lvec, a, e2);
-            else if (a.D == 2) assemble_f32_kernel<2, 1, 0, false><<<grid, threads, 0, s>>>((const float*)lvec, a, e2);
-            else assemble_f32_kernel<3, 1, 0, false><<<grid, threads, 0, s>>>((const float*)lvec, a, e2);
-            return cudaGetLastError();
+            if (a.D == 1) return launch_pdl(assemble_f32_kernel<1, 1, 0, false>, grid, dim3(threads), 0, s, (const float*)lvec, a, e2);
+            if (a.D == 2) return launch_pdl(assemble_f32_kernel<2, 1, 0, false>, grid, dim3(threads), 0, s, (const float*)lvec, a, e2);
+            return launch_pdl(assemble_f32_kernel<3, 1, 0, false>, grid, dim3(threads), 0, s, (const float*)lvec, a, e2);
         }
         EpiF2 e2{};
         for (int o = 0; o < 3; ++o) {
@@ -290,11 +297,11 @@ cudaError_t launch_assemble(bool lvec_fp32, const void* lvec, const AsmArgs& a_i
         e2.nonfinite = ep.nonfinite;
 #define SEMK_F2_NS(D, NO)                                                                                 \
     switch (ep.nsrc) {                                                                                    \
-        case 0: assemble_f32_kernel<D, NO, 0, true><<<grid, threads, 0, s>>>((const float*)lvec, a, e2); break; \
-        case 1: assemble_f32_kernel<D, NO, 1, true><<<grid, threads, 0, s>>>((const float*)lvec, a, e2); break; \
-        case 2: assemble_f32_kernel<D, NO, 2, true><<<grid, threads, 0, s>>>((const float*)lvec, a, e2); break; \
-        case 3: assemble_f32_kernel<D, NO, 3, true><<<grid, threads, 0, s>>>((const float*)lvec, a, e2); break; \
-        default: assemble_f32_kernel<D, NO, 4, true><<<grid, threads, 0, s>>>((const float*)lvec, a, e2); break; \
+        case 0: err = launch_pdl(assemble_f32_kernel<D, NO, 0, true>, grid, dim3(threads), 0, s, (const float*)lvec, a, e2); break; \
+        case 1: err = launch_pdl(assemble_f32_kernel<D, NO, 1, true>, grid, dim3(threads), 0, s, (const float*)lvec, a, e2); break; \
+        case 2: err = launch_pdl(assemble_f32_kernel<D, NO, 2, true>, grid, dim3(threads), 0, s, (const float*)lvec, a, e2); break; \
+        case 3: err = launch_pdl(assemble_f32_kernel<D, NO, 3, true>, grid, dim3(threads), 0, s, (const float*)lvec, a, e2); break; \
+        default: err = launch_pdl(assemble_f32_kernel<D, NO, 4, true>, grid, dim3(threads), 0, s, (const float*)lvec, a, e2); break; \
     }
 #define SEMK_F2_NO(D)                         \
     switch (ep.nout) {                        \
@@ -307,7 +314,7 @@ cudaError_t launch_assemble(bool lvec_fp32, const void* lvec, const AsmArgs& a_i
         else { SEMK_F2_NO(3) }
 #undef SEMK_F2_NO
 #undef SEMK_F2_NS
-        return cudaGetLastError();
+        return err != cudaSuccess ? err : cudaGetLastError();
     } else {
         if (a.D == 1) { SEMK_ASM_NO(double, 1) }
         else if (a.D == 2) { SEMK_ASM_NO(double, 2) }
@@ -315,7 +322,7 @@ cudaError_t launch_assemble(bool lvec_fp32, const void* lvec, const AsmArgs& a_i
     }
 #undef SEMK_ASM_NO
 #undef SEMK_ASM_NS
-    return cudaGetLastError();
+    return err != cudaSuccess ? err : cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ objective

@@ -320,3 +320,20 @@ def test_inviscid_and_zero_fields(prec):
     z = np.zeros_like(u)
     assert float(s.rhs(z).abs().max()) == 0.0          # F(0) = 0 exactly
     assert float(s.jacT(z, z).abs().max()) == 0.0
+
+
+def test_dependent_launch_changes_no_result():
+    """Programmatic dependent launch only overlaps launch latency: the same bits either way."""
+    try:
+        out = []
+        for on in (1, 0):
+            L.lib().sem_set_dependent_launch(on)
+            s = Sem(2, 6, 7, 1e-3)
+            s.use_graph(True)
+            x = s.coords()
+            u0, uo = inputs.workload_field(2, x, 1), inputs.workload_field(2, x, 2)
+            J, g = s.objective_grad(u0, uo, 2e-4, 10, "ssprk3")
+            out.append((J, g.clone(), s.rhs(u0).clone()))
+        assert out[0][0] == out[1][0] and torch.equal(out[0][1], out[1][1]) and torch.equal(out[0][2], out[1][2])
+    finally:
+        L.lib().sem_set_dependent_launch(1)
