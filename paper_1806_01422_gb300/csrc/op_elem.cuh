@@ -86,6 +86,23 @@ __device__ __forceinline__ T tile_value(const ElemArgs& a, const void* g, size_t
     }
 }
 
+// Tile entry of a double input x (FP64 and double-float forms), times 1/k for Z = v / k.
+template <typename T>
+__device__ __forceinline__ T tile_of_double(double x, bool scale_mult, int nb) {
+    if constexpr (std::is_same<T, dfloat>::value) {
+        float h, l;
+        split_bits(x, h, l);
+        if (scale_mult) {
+            const float sc = inv_mult<float>(nb);
+            h *= sc;
+            l *= sc;
+        }
+        return dfloat(h, l);
+    } else {
+        return scale_mult ? x * inv_mult<double>(nb) : x;
+    }
+}
+
 // Load component c of a global field into an element tile (d = 3): thread t of
 // the element owns column (i, j) = (t % n, t / n) and walks k.  `scale_mult`
 // multiplies each node by 1/k (k = elements sharing it), used for Z = v / k.
@@ -100,15 +117,42 @@ __device__ __forceinline__ T load3(T* tile, const void* g, int c, int ex, int ey
     const int nbij = (int)(i == 0 || i == N) + (int)(j == 0 || j == N);
     float ref_hi = 0.f, ref_lo = 0.f;
     if (RefSub<T>::on && !scale_mult && valid) read_pair(a, g, gidx3(c, ez * N, ey * N, ex * N, G), ref_hi, ref_lo);
+    if constexpr (RefSub<T>::on) {
+        // FP32 form: issue every load of the column before the first conversion, so that
+        // the gather's latency is paid once per column rather than once per node
+        float hv[NP], lv[NP];
 #pragma unroll
-    for (int k = 0; k < NP; ++k) {
-        const int gz = wrap(ez * N + k, G);
-        T v = (T)0;
-        if (valid) v = tile_value<T>(a, g, gidx3(c, gz, gy, gx, G), scale_mult,
-                                     nbij + (int)(k == 0 || k == N), ref_hi, ref_lo);
-        tile[(k * NP + j) * Tl::P + i] = v;
+        for (int k = 0; k < NP; ++k) {
+            hv[k] = 0.f;
+            lv[k] = 0.f;
+            const size_t idx = gidx3(c, wrap(ez * N + k, G), gy, gx, G);
+            if (valid) {
+                if (a.in_f2) {
+                    hv[k] = __ldg((const float*)g + idx);
+                    if (!scale_mult) lv[k] = __ldg((const float*)g + a.plane + idx);
+                } else {
+                    split_bits(__ldg((const double*)g + idx), hv[k], lv[k]);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const float v = scale_mult ? hv[k] * inv_mult<float>(nbij + (int)(k == 0 || k == N))
+                                       : __fadd_rn(__fsub_rn(hv[k], ref_hi), __fsub_rn(lv[k], ref_lo));
+            tile[(k * NP + j) * Tl::P + i] = valid ? v : 0.f;
+        }
+        return (T)ref_hi;
+    } else {
+        // double inputs: every load of the column first, then the conversions
+        double xv[NP];
+#pragma unroll
+        for (int k = 0; k < NP; ++k)
+            xv[k] = valid ? __ldg((const double*)g + gidx3(c, wrap(ez * N + k, G), gy, gx, G)) : 0.0;
+#pragma unroll
+        for (int k = 0; k < NP; ++k)
+            tile[(k * NP + j) * Tl::P + i] = tile_of_double<T>(xv[k], scale_mult, nbij + (int)(k == 0 || k == N));
+        return (T)ref_hi;
     }
-    return (T)ref_hi;
 }
 
 // d = 2: thread t owns row j = t and walks i.
@@ -123,14 +167,39 @@ __device__ __forceinline__ T load2(T* tile, const void* g, int c, int ex, int ey
     const size_t row = ((size_t)c * G + gy) * G;
     float ref_hi = 0.f, ref_lo = 0.f;
     if (RefSub<T>::on && !scale_mult && valid) read_pair(a, g, ((size_t)c * G + ey * N) * G + ex * N, ref_hi, ref_lo);
+    if constexpr (RefSub<T>::on) {
+        // every load of the row first, then the conversions (see load3)
+        float hv[NP], lv[NP];
 #pragma unroll
-    for (int i = 0; i < NP; ++i) {
-        const int gx = wrap(ex * N + i, G);
-        T v = (T)0;
-        if (valid) v = tile_value<T>(a, g, row + gx, scale_mult, nbj + (int)(i == 0 || i == N), ref_hi, ref_lo);
-        tile[j * Tl::P + i] = v;
+        for (int i = 0; i < NP; ++i) {
+            hv[i] = 0.f;
+            lv[i] = 0.f;
+            const size_t idx = row + wrap(ex * N + i, G);
+            if (valid) {
+                if (a.in_f2) {
+                    hv[i] = __ldg((const float*)g + idx);
+                    if (!scale_mult) lv[i] = __ldg((const float*)g + a.plane + idx);
+                } else {
+                    split_bits(__ldg((const double*)g + idx), hv[i], lv[i]);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            const float v = scale_mult ? hv[i] * inv_mult<float>(nbj + (int)(i == 0 || i == N))
+                                       : __fadd_rn(__fsub_rn(hv[i], ref_hi), __fsub_rn(lv[i], ref_lo));
+            tile[j * Tl::P + i] = valid ? v : 0.f;
+        }
+        return (T)ref_hi;
+    } else {
+        double xv[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) xv[i] = valid ? __ldg((const double*)g + row + wrap(ex * N + i, G)) : 0.0;
+#pragma unroll
+        for (int i = 0; i < NP; ++i)
+            tile[j * Tl::P + i] = tile_of_double<T>(xv[i], scale_mult, nbj + (int)(i == 0 || i == N));
+        return (T)ref_hi;
     }
-    return (T)ref_hi;
 }
 
 // ================================================================== d = 3
