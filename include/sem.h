@@ -270,10 +270,14 @@ int sem_solver_stats(sem_t h, long long* out4);
  * sem_profile_read waits for the recorded events and returns the summed device
  * time in ms (ms4) and the number of timed launches (count4) per kind:
  * [0] F element kernel, [1] J element kernel, [2] J^T element kernel,
- * [3] gather-scatter assembly; reset != 0 clears them.  Each timed launch costs
- * two event records; the stream waits once per 4096 timed launches. */
+ * [3] gather-scatter assembly; reset != 0 clears them.  bytes4 (may be NULL)
+ * receives the algorithmic bytes of the timed launches, summed the same way:
+ * for the assembly the element-local values read once plus every epilogue
+ * source read and every output written once (8 bytes per unknown each); 0 for
+ * the element kernels.  Each timed launch costs two event records; the stream
+ * waits once per 4096 timed launches. */
 int sem_profile(sem_t h, int every);
-int sem_profile_read(sem_t h, double* ms4, long long* count4, int reset);
+int sem_profile_read(sem_t h, double* ms4, long long* count4, double* bytes4, int reset);
 
 /* ---------------------------------------------------------------- batches
  * Many independent optimisation problems of uneven size (the paper solves one;

@@ -64,7 +64,7 @@ _SIGS = {
     "sem_trajectory_info": (_I, [_H, ctypes.POINTER(ctypes.c_longlong)]),
     "sem_solver_stats": (_I, [_H, ctypes.POINTER(ctypes.c_longlong)]),
     "sem_profile": (_I, [_H, _I]),
-    "sem_profile_read": (_I, [_H, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), _I]),
+    "sem_profile_read": (_I, [_H, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_D), _I]),
     "sem_rhs_noalloc": (_I, [_H, _P, _P, _P]),
     "sem_set_graph": (_I, [_H, _I]),
     "sem_graph_replays": (ctypes.c_longlong, [_H]),

@@ -140,11 +140,13 @@ class Sem:
         L.check(L.lib().sem_profile(self._h, int(every)))
 
     def profile_read(self, reset=True):
-        """{kind: (ms, timed launches)} for kinds rhs, jac, jacT element kernels and assembly."""
+        """{kind: (ms, timed launches, algorithmic bytes)} for kinds rhs, jac, jacT element kernels
+        and assembly (bytes are counted for the assembly only)."""
         ms = (ctypes.c_double * 4)()
         n = (ctypes.c_longlong * 4)()
-        L.check(L.lib().sem_profile_read(self._h, ms, n, 1 if reset else 0))
-        return {k: (ms[i], n[i]) for i, k in enumerate(("rhs", "jac", "jacT", "assemble"))}
+        nb = (ctypes.c_double * 4)()
+        L.check(L.lib().sem_profile_read(self._h, ms, n, nb, 1 if reset else 0))
+        return {k: (ms[i], n[i], nb[i]) for i, k in enumerate(("rhs", "jac", "jacT", "assemble"))}
 
     def sweep_stats(self):
         out = (ctypes.c_longlong * 3)()

@@ -183,6 +183,7 @@ struct sem_ctx {
     bool capturing = false;
     std::vector<cudaEvent_t> gev_start, gev_stop;
     std::vector<int> gev_kind;
+    std::vector<double> gev_bytes;
     // Crank-Nicolson: Newton / GMRES settings, Krylov workspace, counters
     double newton_rtol = 1e-12, krylov_rtol = 1e-12;
     int krylov_m = 30, krylov_maxit = 2000, newton_maxit = 30;
@@ -195,9 +196,11 @@ struct sem_ctx {
     long long prof_tick[4] = {0, 0, 0, 0};
     std::vector<cudaEvent_t> ev_start, ev_stop;
     std::vector<int> ev_kind;
+    std::vector<double> ev_bytes;
     size_t ev_used = 0;
     double prof_ms[4] = {0, 0, 0, 0};
     long long prof_n[4] = {0, 0, 0, 0};
+    double prof_bytes[4] = {0, 0, 0, 0};   // algorithmic bytes of the timed launches
 };
 
 namespace {
@@ -288,13 +291,15 @@ int prof_drain(sem_t h) {
         SEM_CK(cudaEventElapsedTime(&ms, h->ev_start[i], h->ev_stop[i]));
         h->prof_ms[h->ev_kind[i]] += ms;
         h->prof_n[h->ev_kind[i]] += 1;
+        h->prof_bytes[h->ev_kind[i]] += h->ev_bytes[i];
     }
     h->ev_used = 0;
     return SEM_OK;
 }
 
 // Returns the index of the event pair to record around one launch (-1: profiling off).
-int prof_begin(sem_t h, int kind, cudaStream_t s, long long& slot) {
+// bytes: the launch's algorithmic bytes, summed over the timed launches of its kind.
+int prof_begin(sem_t h, int kind, cudaStream_t s, long long& slot, double bytes = 0.0) {
     slot = -1;
     if (!h->prof) return SEM_OK;
     if (h->prof_tick[kind]++ % h->prof != 0) return SEM_OK;
@@ -305,6 +310,7 @@ int prof_begin(sem_t h, int kind, cudaStream_t s, long long& slot) {
         h->gev_start.push_back(a);
         h->gev_stop.push_back(b);
         h->gev_kind.push_back(kind);
+        h->gev_bytes.push_back(bytes);
         slot = -2 - (long long)(h->gev_start.size() - 1);
         // an event recorded into a graph must be an external record node to be timed
         SEM_CK(cudaEventRecordWithFlags(a, s, cudaEventRecordExternal));
@@ -314,6 +320,7 @@ int prof_begin(sem_t h, int kind, cudaStream_t s, long long& slot) {
         h->ev_start.resize(PROF_POOL);
         h->ev_stop.resize(PROF_POOL);
         h->ev_kind.resize(PROF_POOL);
+        h->ev_bytes.resize(PROF_POOL);
         for (size_t i = 0; i < PROF_POOL; ++i) {
             SEM_CK(cudaEventCreate(&h->ev_start[i]));
             SEM_CK(cudaEventCreate(&h->ev_stop[i]));
@@ -322,6 +329,7 @@ int prof_begin(sem_t h, int kind, cudaStream_t s, long long& slot) {
     if (h->ev_used == PROF_POOL) SEM_TRY(prof_drain(h));
     slot = (long long)h->ev_used++;
     h->ev_kind[slot] = kind;
+    h->ev_bytes[slot] = bytes;
     SEM_CK(cudaEventRecord(h->ev_start[slot], s));
     return SEM_OK;
 }
@@ -339,6 +347,7 @@ int prof_graph_accumulate(sem_t h) {
         SEM_CK(cudaEventElapsedTime(&ms, h->gev_start[i], h->gev_stop[i]));
         h->prof_ms[h->gev_kind[i]] += ms;
         h->prof_n[h->gev_kind[i]] += 1;
+        h->prof_bytes[h->gev_kind[i]] += h->gev_bytes[i];
     }
     return SEM_OK;
 }
@@ -351,6 +360,15 @@ void prof_graph_release(sem_t h) {
     h->gev_start.clear();
     h->gev_stop.clear();
     h->gev_kind.clear();
+    h->gev_bytes.clear();
+}
+
+// Algorithmic bytes of one gather-scatter launch: the element-local values read
+// once (FP32 in the FP32-bulk form, FP64 otherwise), every epilogue source read
+// and every output written once, 8 bytes per unknown (FP64, or a float pair).
+double asm_bytes(sem_t h, const Epi& ep) {
+    const double lw = h->precision == SEM_PREC_FP32_BULK ? 4.0 : 8.0;
+    return (double)h->lvec_elems * lw + (double)(ep.nout + ep.nsrc) * (double)h->ndof * 8.0;
 }
 
 // One operator apply: element kernel into the element-local buffer, then the
@@ -404,7 +422,7 @@ int apply(sem_t h, int op, const double* u, const double* w, const Epi& ep, cuda
     if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "element kernel launch: %s", cudaGetErrorString(e));
     SEM_TRY(prof_end(h, slot, s));
     ++h->nlaunch;
-    SEM_TRY(prof_begin(h, 3, s, slot));
+    SEM_TRY(prof_begin(h, 3, s, slot, asm_bytes(h, ep)));
     e = launch_assemble(f32, a.lvec, asm_args(h, op != OP_JACT), ep, s);
     if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "assembly launch: %s", cudaGetErrorString(e));
     SEM_TRY(prof_end(h, slot, s));
@@ -1503,7 +1521,7 @@ int batch_apply(sem_t h, int op, const double* u, const double* w, const Epi& ep
                                       batch_elem_smem(b->threads, op), s);
     if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "batched element kernel: %s", cudaGetErrorString(e));
     SEM_TRY(prof_end(h, slot, s));
-    SEM_TRY(prof_begin(h, 3, s, slot));
+    SEM_TRY(prof_begin(h, 3, s, slot, asm_bytes(h, ep)));
     e = launch_batch_assemble(d, (const double*)h->lvec, op != OP_JACT, ep, s);
     if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "batched assembly: %s", cudaGetErrorString(e));
     SEM_TRY(prof_end(h, slot, s));
@@ -1961,15 +1979,17 @@ int sem_profile(sem_t h, int every) {
     return SEM_OK;
 }
 
-int sem_profile_read(sem_t h, double* ms4, long long* count4, int reset) {
+int sem_profile_read(sem_t h, double* ms4, long long* count4, double* bytes4, int reset) {
     if (!h || !ms4 || !count4) return fail(SEM_ERR_ARG, "null handle or output");
     SEM_TRY(prof_drain(h));
     for (int i = 0; i < 4; ++i) {
         ms4[i] = h->prof_ms[i];
         count4[i] = h->prof_n[i];
+        if (bytes4) bytes4[i] = h->prof_bytes[i];
         if (reset) {
             h->prof_ms[i] = 0;
             h->prof_n[i] = 0;
+            h->prof_bytes[i] = 0;
         }
     }
     return SEM_OK;

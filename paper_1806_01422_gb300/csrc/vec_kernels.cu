@@ -37,84 +37,126 @@ __device__ __forceinline__ A pick4(const A (&t)[4], int k) {
     return k & 2 ? hi : lo;
 }
 
-// The launch grid is (ceil(G / 128), G, d) for d = 2 and (ceil(G / 128), G, d G)
-// for d = 3, so a thread finds its node without integer division (32-bit
-// division and modulo issue conversion instructions on the FP64 pipe); the
-// element index along an axis is a multiply-shift checked on the host.  The y
-// and z coordinates are uniform over a block, so only the x sharing differs
-// between the lanes of a warp: each thread issues the FP64 adds its node needs
-// and no predicated-off ones.  The numbers of epilogue outputs and sources are
-// template parameters for the same reason.
+// Per-axis sharing of a global node index g: owner element e0 = g / N at local
+// index i0 = g % N, left neighbour e1; sh when the node is also e1's node N.
+// The division is a multiply-shift checked on the host (32-bit division and
+// modulo issue conversion instructions on the FP64 pipe).
+struct AxisSplit {
+    int e0, i0, e1;
+    bool sh;
+};
+
+__device__ __forceinline__ AxisSplit axis_split(int g, const AsmArgs& a) {
+    AxisSplit s;
+    s.e0 = (int)(((unsigned)g * a.divN_mul) >> a.divN_shift);
+    s.i0 = g - s.e0 * a.N;
+    s.e1 = s.e0 == 0 ? a.E - 1 : s.e0 - 1;
+    s.sh = s.i0 == 0;
+    return s;
+}
+
+// Sum of the element-local values of component c at one global node, in the
+// fixed order: x pairs first, then y, then z.
+template <typename Acc, typename T, int D>
+__device__ __forceinline__ Acc gather_node(const T* __restrict__ lvec, const AsmArgs& a, int c, unsigned npd,
+                                           const AxisSplit& x, const AxisSplit& y, const AxisSplit& z) {
+    auto L = [&](int ex, int ix, int ey, int iy, int ez, int iz) -> Acc {
+        const unsigned el = ((unsigned)ez * a.E + ey) * a.E + ex;
+        const unsigned node = ((unsigned)iz * a.NP + iy) * a.NP + ix;
+        return lvec[((size_t)el * D + c) * npd + node];
+    };
+    Acc sum = L(x.e0, x.i0, y.e0, y.i0, z.e0, z.i0);
+    if (x.sh) sum += L(x.e1, a.N, y.e0, y.i0, z.e0, z.i0);
+    if (D >= 2 && y.sh) {
+        Acc t = L(x.e0, x.i0, y.e1, a.N, z.e0, z.i0);
+        if (x.sh) t += L(x.e1, a.N, y.e1, a.N, z.e0, z.i0);
+        sum += t;
+    }
+    if (D >= 3 && z.sh) {
+        Acc t = L(x.e0, x.i0, y.e0, y.i0, z.e1, a.N);
+        if (x.sh) t += L(x.e1, a.N, y.e0, y.i0, z.e1, a.N);
+        if (y.sh) {
+            Acc t2 = L(x.e0, x.i0, y.e1, a.N, z.e1, a.N);
+            if (x.sh) t2 += L(x.e1, a.N, y.e1, a.N, z.e1, a.N);
+            t += t2;
+        }
+        sum += t;
+    }
+    return sum;
+}
+
+// Node rows (along y) per thread: in 3D each thread gathers and combines
+// asm_rows(3) nodes with independent loads, which halves the number of blocks
+// (each with a partly idle last warp when G is not a multiple of 32).
+// Measured on GB300 this shortens the 3D assembly by about a sixth; four rows
+// gained nothing, and in 2D one row per thread measured faster.
+constexpr int ASM_ROWS_3D = 2;
+__host__ __device__ constexpr int asm_rows(int D) { return D == 3 ? ASM_ROWS_3D : 1; }
+
+// The launch grid is (ceil(G / 128), G, d) for d = 2 and
+// (ceil(G / 128), ceil(G / R), d G) for d = 3 with R = asm_rows(3), so a
+// thread finds its nodes without integer division.  The y and z coordinates are
+// uniform over a block, so only the x sharing differs between the lanes of a
+// warp: each thread issues the FP64 adds its nodes need and no predicated-off
+// ones.  The numbers of epilogue outputs and sources are template parameters
+// for the same reason.  A row past the end (G not a multiple of R) repeats the
+// block's first row and stores nothing.
 template <typename T, int D, int NOUT, int NSRC>
 __global__ void __launch_bounds__(128) assemble_kernel(const T* __restrict__ lvec, const AsmArgs a,
                                                        const Epi ep) {
     pdl_wait();
     const int gx = blockIdx.x * blockDim.x + threadIdx.x;
     if (gx >= a.G) return;
-    int gy = 0, gz = 0, c = 0;
+    constexpr int R = asm_rows(D);
+    int gy0 = 0, gz = 0, c = 0;
     if (D == 2) {
-        gy = blockIdx.y;
+        gy0 = blockIdx.y * R;
         c = blockIdx.z;
     } else if (D == 3) {
-        gy = blockIdx.y;
+        gy0 = blockIdx.y * R;
         c = blockIdx.z / a.G;          // once per block: blockIdx.z < 3G
         gz = blockIdx.z - c * a.G;
     }
-    const unsigned idx = c * a.GD + ((unsigned)gz * a.G + gy) * a.G + gx;
     const unsigned npd = D == 1 ? a.NP : (D == 2 ? a.NP * a.NP : a.NP * a.NP * a.NP);
-    auto split = [&](int g, int& e0, int& i0, int& e1) {
-        e0 = (int)(((unsigned)g * a.divN_mul) >> a.divN_shift);
-        i0 = g - e0 * a.N;
-        e1 = e0 == 0 ? a.E - 1 : e0 - 1;
-        return i0 == 0;
-    };
-    int ex0, ix0, ex1, ey0 = 0, iy0 = 0, ey1 = 0, ez0 = 0, iz0 = 0, ez1 = 0;
-    const bool shx = split(gx, ex0, ix0, ex1);
-    const bool shy = D >= 2 ? split(gy, ey0, iy0, ey1) : false;
-    const bool shz = D >= 3 ? split(gz, ez0, iz0, ez1) : false;
-    const int nsh = (int)shx + (int)shy + (int)shz;
-    // value of element (ex, ey, ez) at local node (ix, iy, iz)
-    auto L = [&](int ex, int ix, int ey, int iy, int ez, int iz) -> T {
-        const unsigned el = ((unsigned)ez * a.E + ey) * a.E + ex;
-        const unsigned node = ((unsigned)iz * a.NP + iy) * a.NP + ix;
-        return lvec[((size_t)el * D + c) * npd + node];
-    };
-    // fixed summation order: x pairs first, then y, then z
-    using Acc = typename std::conditional<sizeof(T) == 8, double, float>::type;
-    Acc sum = L(ex0, ix0, ey0, iy0, ez0, iz0);
-    if (shx) sum += L(ex1, a.N, ey0, iy0, ez0, iz0);
-    if (D >= 2 && shy) {
-        Acc t = L(ex0, ix0, ey1, a.N, ez0, iz0);
-        if (shx) t += L(ex1, a.N, ey1, a.N, ez0, iz0);
-        sum += t;
-    }
-    if (D >= 3 && shz) {
-        Acc t = L(ex0, ix0, ey0, iy0, ez1, a.N);
-        if (shx) t += L(ex1, a.N, ey0, iy0, ez1, a.N);
-        if (shy) {
-            Acc t2 = L(ex0, ix0, ey1, a.N, ez1, a.N);
-            if (shx) t2 += L(ex1, a.N, ey1, a.N, ez1, a.N);
-            t += t2;
-        }
-        sum += t;
-    }
-    const double sumd = (double)sum;
-    // read every source before writing any output: an output may be a source (in place)
-    double sv[NSRC > 0 ? NSRC : 1];
+    const AxisSplit none{0, 0, 0, false};
+    const AxisSplit sx = axis_split(gx, a);
+    const AxisSplit sz = D >= 3 ? axis_split(gz, a) : none;
+    double sum[R];
+    unsigned idx[R];
+    int nsh[R];
+    bool live[R];
 #pragma unroll
-    for (int m = 0; m < NSRC; ++m) sv[m] = ep.src[m][idx];
-    double ov[NOUT];
+    for (int r = 0; r < R; ++r) {
+        live[r] = r == 0 || gy0 + r < a.G;   // uniform over the block
+        const int gy = live[r] ? gy0 + r : gy0;
+        const AxisSplit sy = D >= 2 ? axis_split(gy, a) : none;
+        sum[r] = gather_node<double, T, D>(lvec, a, c, npd, sx, sy, sz);
+        nsh[r] = (int)sx.sh + (int)sy.sh + (int)sz.sh;
+        idx[r] = c * a.GD + ((unsigned)gz * a.G + gy) * a.G + gx;
+    }
+    // read every source before writing any output: an output may be a source (in place)
+    double sv[R][NSRC > 0 ? NSRC : 1];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int m = 0; m < NSRC; ++m) sv[r][m] = ep.src[m][idx[r]];
+    double ov[R][NOUT];
     bool bad = false;
 #pragma unroll
-    for (int o = 0; o < NOUT; ++o) {
-        double v = pick4(ep.alpha_k[o], nsh) * sumd;
+    for (int r = 0; r < R; ++r)
 #pragma unroll
-        for (int m = 0; m < NSRC; ++m) v = fma(ep.beta[o][m], sv[m], v);
-        ov[o] = v;
-        bad |= nonfinite_bits(v);
-    }
+        for (int o = 0; o < NOUT; ++o) {
+            double v = pick4(ep.alpha_k[o], nsh[r]) * sum[r];
 #pragma unroll
-    for (int o = 0; o < NOUT; ++o) ep.out[o][idx] = ov[o];
+            for (int m = 0; m < NSRC; ++m) v = fma(ep.beta[o][m], sv[r][m], v);
+            ov[r][o] = v;
+            bad |= live[r] && nonfinite_bits(v);
+        }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+        if (live[r])
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o) ep.out[o][idx[r]] = ov[r][o];
     if (bad && ep.nonfinite) atomicOr(ep.nonfinite, 1u);
 }
 
@@ -138,74 +180,73 @@ __global__ void __launch_bounds__(128) assemble_f32_kernel(const float* __restri
     pdl_wait();
     const int gx = blockIdx.x * blockDim.x + threadIdx.x;
     if (gx >= a.G) return;
-    int gy = 0, gz = 0, c = 0;
+    constexpr int R = asm_rows(D);
+    int gy0 = 0, gz = 0, c = 0;
     if (D == 2) {
-        gy = blockIdx.y;
+        gy0 = blockIdx.y * R;
         c = blockIdx.z;
     } else if (D == 3) {
-        gy = blockIdx.y;
+        gy0 = blockIdx.y * R;
         c = blockIdx.z / a.G;
         gz = blockIdx.z - c * a.G;
     }
-    const unsigned idx = c * a.GD + ((unsigned)gz * a.G + gy) * a.G + gx;
     const unsigned npd = D == 1 ? a.NP : (D == 2 ? a.NP * a.NP : a.NP * a.NP * a.NP);
-    auto split = [&](int g, int& e0, int& i0, int& e1) {
-        e0 = (int)(((unsigned)g * a.divN_mul) >> a.divN_shift);
-        i0 = g - e0 * a.N;
-        e1 = e0 == 0 ? a.E - 1 : e0 - 1;
-        return i0 == 0;
-    };
-    int ex0, ix0, ex1, ey0 = 0, iy0 = 0, ey1 = 0, ez0 = 0, iz0 = 0, ez1 = 0;
-    const bool shx = split(gx, ex0, ix0, ex1);
-    const bool shy = D >= 2 ? split(gy, ey0, iy0, ey1) : false;
-    const bool shz = D >= 3 ? split(gz, ez0, iz0, ez1) : false;
-    const int nsh = (int)shx + (int)shy + (int)shz;
-    auto L = [&](int ex, int ix, int ey, int iy, int ez, int iz) -> float {
-        const unsigned el = ((unsigned)ez * a.E + ey) * a.E + ex;
-        const unsigned node = ((unsigned)iz * a.NP + iy) * a.NP + ix;
-        return lvec[((size_t)el * D + c) * npd + node];
-    };
-    float sum = L(ex0, ix0, ey0, iy0, ez0, iz0);
-    if (shx) sum += L(ex1, a.N, ey0, iy0, ez0, iz0);
-    if (D >= 2 && shy) {
-        float t = L(ex0, ix0, ey1, a.N, ez0, iz0);
-        if (shx) t += L(ex1, a.N, ey1, a.N, ez0, iz0);
-        sum += t;
-    }
-    if (D >= 3 && shz) {
-        float t = L(ex0, ix0, ey0, iy0, ez1, a.N);
-        if (shx) t += L(ex1, a.N, ey0, iy0, ez1, a.N);
-        if (shy) {
-            float t2 = L(ex0, ix0, ey1, a.N, ez1, a.N);
-            if (shx) t2 += L(ex1, a.N, ey1, a.N, ez1, a.N);
-            t += t2;
-        }
-        sum += t;
+    const AxisSplit none{0, 0, 0, false};
+    const AxisSplit sx = axis_split(gx, a);
+    const AxisSplit sz = D >= 3 ? axis_split(gz, a) : none;
+    float sum[R];
+    unsigned idx[R];
+    int nsh[R];
+    bool live[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        live[r] = r == 0 || gy0 + r < a.G;
+        const int gy = live[r] ? gy0 + r : gy0;
+        const AxisSplit sy = D >= 2 ? axis_split(gy, a) : none;
+        sum[r] = gather_node<float, float, D>(lvec, a, c, npd, sx, sy, sz);
+        nsh[r] = (int)sx.sh + (int)sy.sh + (int)sz.sh;
+        idx[r] = c * a.GD + ((unsigned)gz * a.G + gy) * a.G + gx;
     }
     if constexpr (!F2) {
         // plain apply: alpha = 1, no sources; 1/k (F and J only) is an exact power of two
-        const float v = a.scale_mult ? sum * (nsh == 0 ? 1.f : (nsh == 1 ? 0.5f : (nsh == 2 ? 0.25f : 0.125f))) : sum;
-        ep.out_f64[idx] = widen_bits(v);
-        if (nonfinite_f(v) && ep.nonfinite) atomicOr(ep.nonfinite, 1u);
-    } else {
-        df sv[NSRC > 0 ? NSRC : 1];
-#pragma unroll
-        for (int m = 0; m < NSRC; ++m) sv[m] = {ep.src[m][idx], ep.src[m][ep.plane + idx]};
-        df ov[NOUT];
         bool bad = false;
 #pragma unroll
-        for (int o = 0; o < NOUT; ++o) {
-            df v = df_mul_f(pick4(ep.alpha_k[o], nsh), sum);
-#pragma unroll
-            for (int m = 0; m < NSRC; ++m) v = df_add(v, df_mul(ep.beta[o][m], sv[m]));
-            ov[o] = v;
-            bad |= nonfinite_f(v.hi);
+        for (int r = 0; r < R; ++r) {
+            const int k = nsh[r];
+            const float v = a.scale_mult ? sum[r] * (k == 0 ? 1.f : (k == 1 ? 0.5f : (k == 2 ? 0.25f : 0.125f)))
+                                         : sum[r];
+            if (live[r]) {
+                ep.out_f64[idx[r]] = widen_bits(v);
+                bad |= nonfinite_f(v);
+            }
         }
+        if (bad && ep.nonfinite) atomicOr(ep.nonfinite, 1u);
+    } else {
+        df sv[R][NSRC > 0 ? NSRC : 1];
 #pragma unroll
-        for (int o = 0; o < NOUT; ++o) {
-            ep.out[o][idx] = ov[o].hi;
-            ep.out[o][ep.plane + idx] = ov[o].lo;
-        }
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int m = 0; m < NSRC; ++m) sv[r][m] = {ep.src[m][idx[r]], ep.src[m][ep.plane + idx[r]]};
+        df ov[R][NOUT];
+        bool bad = false;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o) {
+                df v = df_mul_f(pick4(ep.alpha_k[o], nsh[r]), sum[r]);
+#pragma unroll
+                for (int m = 0; m < NSRC; ++m) v = df_add(v, df_mul(ep.beta[o][m], sv[r][m]));
+                ov[r][o] = v;
+                bad |= live[r] && nonfinite_f(v.hi);
+            }
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (live[r])
+#pragma unroll
+                for (int o = 0; o < NOUT; ++o) {
+                    ep.out[o][idx[r]] = ov[r][o].hi;
+                    ep.out[o][ep.plane + idx[r]] = ov[r][o].lo;
+                }
         if (bad && ep.nonfinite) atomicOr(ep.nonfinite, 1u);
     }
 }
@@ -253,10 +294,10 @@ cudaError_t launch_assemble(bool lvec_fp32, const void* lvec, const AsmArgs& a_i
     const int threads = 128;
     dim3 grid((a.G + threads - 1) / threads, 1, 1);
     if (a.D == 2) {
-        grid.y = a.G;
+        grid.y = (a.G + asm_rows(2) - 1) / asm_rows(2);
         grid.z = 2;
     } else if (a.D == 3) {
-        grid.y = a.G;
+        grid.y = (a.G + asm_rows(3) - 1) / asm_rows(3);
         grid.z = 3 * a.G;
     }
     if (ep.nout < 1 || ep.nout > 3 || ep.nsrc < 0 || ep.nsrc > 4) return cudaErrorInvalidValue;

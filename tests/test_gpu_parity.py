@@ -297,6 +297,27 @@ def test_kernel_timing_inside_a_replayed_graph():
     assert second["rhs"][1] == 6 and second["jacT"][1] == 6 and second["assemble"][1] == 12
     assert first["rhs"][1] == second["rhs"][1]
     assert all(second[k][0] > 0 for k in ("rhs", "jacT", "assemble"))
+    # every timed assembly reads the element-local values and writes at least one output
+    d, E, N = 2, 6, 7
+    lvec, ndof = d * (E * (N + 1)) ** d * 8, d * (E * N) ** d
+    assert lvec + ndof * 8 <= second["assemble"][2] / 12 <= lvec + 7 * ndof * 8
+
+
+@pytest.mark.parametrize("prec,lw", [("fp64", 8), ("fp32_bulk", 4)])
+@pytest.mark.parametrize("dim,E,N", [(2, 6, 7), (3, 3, 5)])
+def test_assembly_bytes_of_timed_applies(dim, E, N, prec, lw):
+    """The library counts the algorithmic bytes of each timed assembly: the element-local values
+    once, plus 8 bytes per unknown for each epilogue source and output."""
+    s, g = pair(dim, E, N, precision=prec)
+    u = torch.from_numpy(smooth(g, 1)).cuda()
+    s.profile(1)
+    s.rhs(u)
+    s.jacT(u, u)
+    p = s.profile_read(reset=True)
+    lvec, ndof = dim * (E * (N + 1)) ** dim * lw, dim * (E * N) ** dim
+    assert p["assemble"][1] == 2 and p["assemble"][2] == 2 * (lvec + ndof * 8)
+    assert p["rhs"][1] == 1 and p["rhs"][2] == 0 and p["jacT"][1] == 1
+    s.profile(0)
 
 
 # Degenerate cases: the lowest order (two points per direction), no viscosity, the zero field.
