@@ -548,8 +548,8 @@ int rk_adjoint_step(sem_t h, const Tableau& T, double dt, const double* const* Y
             std::memset(&ep, 0, sizeof(ep));
             ep.nonfinite = h->flag;
             ep.f2 = f32(h);
-            const int sl = add_src(ep, lam);
             if (i > 0) {
+                const int sl = add_src(ep, lam);
                 ep.out[0] = nu;
                 ep.alpha[0] = dt * T.A[i][i - 1];
                 ep.beta[0][sl] = dt * T.b[i - 1];

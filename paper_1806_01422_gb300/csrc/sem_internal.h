@@ -23,7 +23,10 @@ void set_pdl(bool on);   // programmatic dependent launch of element and assembl
 // Epilogue of the gather-scatter sum: for each unique scalar node with
 // assembled value a,  out[o] = alpha[o] a + sum_m beta[o][m] src[m]  (o < nout).
 // The host fills alpha; the launcher folds the 1/k multiplicity of F and J
-// into alpha_k[o][nsh] = alpha[o] / 2^nsh so the kernel spends one multiply.
+// into alpha_k[o][nsh] = alpha[o] / 2^nsh so the kernel spends one multiply,
+// and sets key[o]: bit m when beta[o][m] != 0, bit 4 when alpha_k[o][*] == 1.
+// The FP64 assembly skips the zero terms and the unit multiply (both exact);
+// the float-pair assembly of the FP32-bulk form computes every term.
 struct Epi {
     double* out[3];
     double alpha[3];
@@ -33,6 +36,7 @@ struct Epi {
     unsigned* nonfinite;  // set to 1 if any output is NaN/Inf (may be null)
     int f2;               // FP32 form: out/src are float-pair planes (lo plane at +ndof floats)
     double alpha_k[3][4]; // filled by launch_assemble
+    unsigned key[3];      // filled by launch_assemble
 };
 
 struct AsmArgs {

@@ -85,6 +85,50 @@ __device__ __forceinline__ Acc gather_node(const T* __restrict__ lvec, const Asm
     return sum;
 }
 
+// The terms of one RK-epilogue output are fixed at compile time by KEY: bit m
+// when source m enters (beta != 0), bit 4 when alpha_k == 1 (no 1/k scaling);
+// v = alpha_k a + sum over the set bits of beta_m src_m, in source order.  The
+// host builds the key per launch, so the switch below is a branch that every
+// thread takes the same way, and a skipped term issues no instruction: a
+// predicated-off FP64 instruction would still occupy the FP64 pipe.  Leaving
+// out a zero term or a unit multiply does not change the result.
+#define SEMK_KEY_CASES(X)                                                                    \
+    X(0) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15)   \
+    X(16) X(17) X(18) X(19) X(20) X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29)     \
+    X(30) X(31)
+
+template <int R, int NSRC, unsigned KEY>
+__device__ __forceinline__ void epi_terms(double (&v)[R], const double (&a)[R], const double (&sum)[R],
+                                          const double (&b)[4], const double (&sv)[R][NSRC > 0 ? NSRC : 1]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        double x = (KEY & 16u) ? sum[r] : a[r] * sum[r];
+#pragma unroll
+        for (int m = 0; m < NSRC; ++m)
+            if ((KEY >> m) & 1u) x = fma(b[m], sv[r][m], x);
+        v[r] = x;
+    }
+}
+
+template <int R, int NSRC>
+__device__ __forceinline__ void epi_output(unsigned key, double (&v)[R], const double (&a)[R],
+                                           const double (&sum)[R], const double (&b)[4],
+                                           const double (&sv)[R][NSRC > 0 ? NSRC : 1]) {
+    constexpr unsigned FULL = (1u << NSRC) - 1u;
+    switch (key) {
+#define SEMK_EPI_CASE(K)                                                     \
+    case K:                                                                  \
+        if constexpr ((K & 15u) <= FULL) {                                   \
+            epi_terms<R, NSRC, K>(v, a, sum, b, sv);                         \
+            return;                                                          \
+        }                                                                    \
+        break;
+        SEMK_KEY_CASES(SEMK_EPI_CASE)
+#undef SEMK_EPI_CASE
+    }
+    epi_terms<R, NSRC, FULL>(v, a, sum, b, sv);   // not reached: keys come from the sources
+}
+
 // Node rows (along y) per thread: in 3D each thread gathers and combines
 // asm_rows(3) nodes with independent loads, which halves the number of blocks
 // (each with a partly idle last warp when G is not a multiple of 32).
@@ -143,15 +187,17 @@ __global__ void __launch_bounds__(128) assemble_kernel(const T* __restrict__ lve
     double ov[R][NOUT];
     bool bad = false;
 #pragma unroll
-    for (int r = 0; r < R; ++r)
+    for (int o = 0; o < NOUT; ++o) {
+        double ak[R], v[R];
 #pragma unroll
-        for (int o = 0; o < NOUT; ++o) {
-            double v = pick4(ep.alpha_k[o], nsh[r]) * sum[r];
+        for (int r = 0; r < R; ++r) ak[r] = pick4(ep.alpha_k[o], nsh[r]);
+        epi_output<R, NSRC>(ep.key[o], v, ak, sum, ep.beta[o], sv);
 #pragma unroll
-            for (int m = 0; m < NSRC; ++m) v = fma(ep.beta[o][m], sv[r][m], v);
-            ov[r][o] = v;
-            bad |= live[r] && nonfinite_bits(v);
+        for (int r = 0; r < R; ++r) {
+            ov[r][o] = v[r];
+            bad |= live[r] && nonfinite_bits(v[r]);
         }
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r)
         if (live[r])
@@ -227,6 +273,8 @@ __global__ void __launch_bounds__(128) assemble_f32_kernel(const float* __restri
         for (int r = 0; r < R; ++r)
 #pragma unroll
             for (int m = 0; m < NSRC; ++m) sv[r][m] = {ep.src[m][idx[r]], ep.src[m][ep.plane + idx[r]]};
+        // every term, zero or not: skipping them by key (as the FP64 kernel does)
+        // measured slower here, where the FP32 pipe has room to spare
         df ov[R][NOUT];
         bool bad = false;
 #pragma unroll
@@ -278,8 +326,13 @@ static bool magic_div(int N, int G, unsigned& mul, int& shift) {
 cudaError_t launch_assemble(bool lvec_fp32, const void* lvec, const AsmArgs& a_in, const Epi& ep_in,
                             cudaStream_t s) {
     Epi ep = ep_in;
-    for (int o = 0; o < 3; ++o)
+    for (int o = 0; o < 3; ++o) {
         for (int k = 0; k < 4; ++k) ep.alpha_k[o][k] = a_in.scale_mult ? ep.alpha[o] / (double)(1 << k) : ep.alpha[o];
+        unsigned key = !a_in.scale_mult && ep.alpha[o] == 1.0 ? 16u : 0u;
+        for (int m = 0; m < ep.nsrc && m < 4; ++m)
+            if (ep.beta[o][m] != 0.0) key |= 1u << m;
+        ep.key[o] = key;
+    }
     AsmArgs a = a_in;
     if (a.G <= 0) return cudaSuccess;
     thread_local int cN = -1, cG = -1, cShift = 0;
