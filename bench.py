@@ -79,7 +79,7 @@ TRAFFIC = {
         "capture": "dram__bytes_read.sum + dram__bytes_write.sum of one jact2 launch at 64x64 quads, N=7 "
                    "(ncu --set full; profiles/rhs2_jact2_assemble_2d_fp64_E64_N7.md)"},
     "op2c_kernel<semk::dfa::dfloat,8> (J^T)@2d@fp64_df": {
-        "bytes": 6529792 + 0, "src": "a16d1fe8a8f9f7aa",
+        "bytes": 6534656 + 0, "src": "a16d1fe8a8f9f7aa",
         "capture": "dram__bytes_read.sum + dram__bytes_write.sum of one J^T launch (op2c_kernel) at 64x64 "
                    "quads, N=7 (ncu --set full; profiles/rhs2_jact2_2d_fp64df_E64_N7.md)"},
 }
