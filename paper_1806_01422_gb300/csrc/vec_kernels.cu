@@ -19,7 +19,8 @@
 namespace semk {
 
 // FP64 work per unique node: (contributions - 1) adds, then per output one
-// multiply and one fused multiply-add per source.  The FP64 pipe of GB300 issues
+// multiply (none when alpha is 1) and one fused multiply-add per source with a
+// nonzero coefficient (epi_output below).  The FP64 pipe of GB300 issues
 // two lanes per SM per clock, so everything else (the non-finite test on the
 // exponent bits, the choice of contributions, the index arithmetic) stays on the
 // integer pipes.
