@@ -88,7 +88,7 @@ TRAFFIC = {
 KERNEL_SOURCES = {"elem": ["op_kernels.cuh", "op_elem.cuh", "op_elem_lean.cuh", "op_launch.cuh", "df64.cuh",
                            "op_d1.cu", "op_d2.cu", "op_d2_df.cu", "op_d3.cu", "op_d3_f.cu", "op_d3_df.cu",
                            "op_d3_df_mid.cu", "op_d3_df_hi.cu"],
-                  "assemble": ["vec_kernels.cu", "df64.cuh"]}
+                  "assemble": ["vec_kernels.cu", "asm_epi.cuh", "df64.cuh"]}
 
 
 def kernel_src_hash(family):

@@ -10,6 +10,7 @@
 // the packed vectors; only the operator applies and the misfit differ.
 #include <type_traits>
 
+#include "asm_epi.cuh"
 #include "op_launch.cuh"
 #include "sem_internal.h"
 
@@ -133,18 +134,19 @@ __global__ void __launch_bounds__(128) batch_asm2_kernel(const double* __restric
         }
         const int nsh = (int)shx + (int)shy;
         const unsigned idx = in.off + c * in.GD + (unsigned)gy * G + gx;
-        double sv[NSRC > 0 ? NSRC : 1];
+        double sv[1][NSRC > 0 ? NSRC : 1];
 #pragma unroll
-        for (int m = 0; m < NSRC; ++m) sv[m] = ep.src[m][idx];
+        for (int m = 0; m < NSRC; ++m) sv[0][m] = ep.src[m][idx];
         double ov[NOUT];
         bool bad = false;
+        const double s1[1] = {sum};
 #pragma unroll
         for (int o = 0; o < NOUT; ++o) {
-            double v = ep.alpha_k[o][nsh] * sum;
-#pragma unroll
-            for (int m = 0; m < NSRC; ++m) v = fma(ep.beta[o][m], sv[m], v);
-            ov[o] = v;
-            bad |= (__double2hiint(v) & 0x7ff00000) == 0x7ff00000;
+            const double ak[1] = {pick4(ep.alpha_k[o], nsh)};
+            double v[1];
+            epi_output<1, NSRC>(ep.key[o], v, ak, s1, ep.beta[o], sv);
+            ov[o] = v[0];
+            bad |= nonfinite_bits(v[0]);
         }
 #pragma unroll
         for (int o = 0; o < NOUT; ++o) ep.out[o][idx] = ov[o];
@@ -155,8 +157,7 @@ __global__ void __launch_bounds__(128) batch_asm2_kernel(const double* __restric
 cudaError_t launch_batch_assemble(const BatchDev& b, const double* lvec, int scale_mult, const Epi& ep_in,
                                   cudaStream_t s) {
     Epi ep = ep_in;
-    for (int o = 0; o < 3; ++o)
-        for (int k = 0; k < 4; ++k) ep.alpha_k[o][k] = scale_mult ? ep.alpha[o] / (double)(1 << k) : ep.alpha[o];
+    epi_prepare(ep, scale_mult);
     if (b.nrows <= 0) return cudaSuccess;
     if (ep.nout < 1 || ep.nout > 3 || ep.nsrc < 0 || ep.nsrc > 4) return cudaErrorInvalidValue;
 #define SEMK_BA_NS(NO)                                                                             \
