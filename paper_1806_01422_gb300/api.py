@@ -22,6 +22,17 @@ def _stream(device):
     return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
 
 
+def _device(device):
+    """The handle's device with an explicit index (a bare "cuda" means the current device)."""
+    if device is None:
+        return torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available() \
+            else torch.device("cpu")
+    device = torch.device(device)
+    if device.type == "cuda" and device.index is None:
+        device = torch.device("cuda", torch.cuda.current_device())
+    return device
+
+
 class Sem:
     """Periodic d-dimensional viscous Burgers on E^d GLL elements of order N (one GPU)."""
 
@@ -37,8 +48,7 @@ class Sem:
         self.G = E * N
         self.ndof = int(L.lib().sem_ndof(h))
         self.shape = (dim,) + (self.G,) * dim
-        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device()) \
-            if torch.cuda.is_available() else torch.device("cpu")
+        self.device = _device(device)
 
     # ------------------------------------------------------------ lifetime
     def close(self):
@@ -70,9 +80,22 @@ class Sem:
             raise TypeError("%s must be float64" % name)
         if t.numel() != self.ndof:
             raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), self.ndof))
-        if t.device.type != "cuda":
+        if t.device != self.device:
             t = t.to(self.device, non_blocking=t.is_pinned())
         return t.contiguous().view(self.shape)
+
+    def _out(self, t, name):
+        """A caller's output buffer, written in place by the library: it must already be a
+        contiguous float64 tensor of ndof values on the handle's device (None: a new one)."""
+        if t is None:
+            return self.empty()
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64:
+            raise TypeError("%s must be a float64 tensor" % name)
+        if t.device != self.device:
+            raise ValueError("%s is on %s, the handle on %s" % (name, t.device, self.device))
+        if t.numel() != self.ndof or not t.is_contiguous():
+            raise ValueError("%s must be contiguous with %d elements" % (name, self.ndof))
+        return t
 
     @staticmethod
     def _p(t):
@@ -81,38 +104,39 @@ class Sem:
     # ------------------------------------------------------------ operators
     def rhs(self, u, out=None):
         u = self._dev(u, "u")
-        out = self.empty() if out is None else out
+        out = self._out(out, "out")
         L.check(L.lib().sem_rhs(self._h, self._p(u), self._p(out), _stream(self.device)))
         return out
 
     def jac(self, u, w, out=None):
         u, w = self._dev(u, "u"), self._dev(w, "w")
-        out = self.empty() if out is None else out
+        out = self._out(out, "out")
         L.check(L.lib().sem_jac_apply(self._h, self._p(u), self._p(w), self._p(out), _stream(self.device)))
         return out
 
     def jacT(self, u, v, out=None):
         u, v = self._dev(u, "u"), self._dev(v, "v")
-        out = self.empty() if out is None else out
+        out = self._out(out, "out")
         L.check(L.lib().sem_jacT_apply(self._h, self._p(u), self._p(v), self._p(out), _stream(self.device)))
         return out
 
     # ------------------------------------------------------------ sweeps
     def rk_forward(self, u0, dt, nsteps, scheme="rk4", out=None):
         u0 = self._dev(u0, "u0")
-        out = self.empty() if out is None else out
+        out = self._out(out, "out")
         L.check(L.lib().sem_rk_forward(self._h, SCHEMES[scheme], float(dt), int(nsteps), self._p(u0),
                                        self._p(out), _stream(self.device)))
         return out
 
     def rk_adjoint(self, lamT, out=None):
         lamT = self._dev(lamT, "lamT")
-        out = self.empty() if out is None else out
+        out = self._out(out, "out")
         L.check(L.lib().sem_rk_adjoint(self._h, self._p(lamT), self._p(out), _stream(self.device)))
         return out
 
     def objective(self, u, u_obs, lam=None):
         u, u_obs = self._dev(u, "u"), self._dev(u_obs, "u_obs")
+        lam = self._out(lam, "lam") if lam is not None else None
         J = ctypes.c_double()
         L.check(L.lib().sem_objective(self._h, self._p(u), self._p(u_obs), ctypes.byref(J),
                                       self._p(lam) if lam is not None else None, _stream(self.device)))
@@ -121,7 +145,7 @@ class Sem:
     def objective_grad(self, u0, u_obs, dt, nsteps, scheme="rk4", grad=None, host=False):
         """(J, dJ/du0).  With host=True the gradient is returned as a CPU tensor."""
         u0, u_obs = self._dev(u0, "u0"), self._dev(u_obs, "u_obs")
-        grad = self.empty() if grad is None else grad
+        grad = self._out(grad, "grad")
         J = ctypes.c_double()
         L.check(L.lib().sem_objective_grad(self._h, SCHEMES[scheme], float(dt), int(nsteps), self._p(u0),
                                            self._p(u_obs), ctypes.byref(J), self._p(grad),
@@ -230,8 +254,7 @@ class SemBatch(Sem):
             off, n = ctypes.c_size_t(), ctypes.c_size_t()
             L.check(L.lib().sem_batch_layout(h, k, ctypes.byref(off), ctypes.byref(n)))
             self.layout.append((off.value, n.value))
-        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device()) \
-            if torch.cuda.is_available() else torch.device("cpu")
+        self.device = _device(device)
 
     def coords(self, k):
         x = np.empty(self.E[k] * self.N[k])
@@ -258,7 +281,7 @@ class SemBatch(Sem):
     def objective_grad_each(self, u0, u_obs, dt, nsteps, scheme="rk4", grad=None):
         """(per-instance misfits, packed gradient)."""
         u0, u_obs = self._dev(u0, "u0"), self._dev(u_obs, "u_obs")
-        grad = self.empty() if grad is None else grad
+        grad = self._out(grad, "grad")
         J = (ctypes.c_double * self.count)()
         L.check(L.lib().sem_batch_objective_grad(self._h, SCHEMES[scheme], float(dt), int(nsteps), self._p(u0),
                                                  self._p(u_obs), J, self._p(grad), _stream(self.device)))
