@@ -316,17 +316,21 @@ int sem_batch_objective_grad(sem_t h, int scheme, double dt, int nsteps,
 /* Size of the fixed device array used by sem_rhs_noalloc (16 MiB). */
 #define SEM_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
 
-/* f = F(u) exactly as sem_rhs computes it, but without allocating any device
- * memory (the paper has no counterpart; this serves callers that cannot call
- * cudaMalloc, e.g. hosts whose device memory belongs to their own pool, or
- * loops that must not take the synchronisation an allocation can cause).
+/* f = F(u) exactly as sem_rhs computes it (the element kernels of the handle's
+ * precision: FP64, FP64-DF or FP32-bulk, and the same gather-scatter), but
+ * without allocating any device memory.  The paper has no counterpart; this
+ * serves callers that cannot call cudaMalloc, e.g. hosts whose device memory
+ * belongs to their own pool, or loops that must not take the synchronisation
+ * an allocation can cause.  It works on a handle that has not yet allocated
+ * its own workspace.
  * The element-local scratch is a file-scope device array of
  * SEM_NOALLOC_SCRATCH_BYTES on every GPU that loads the library, kept until the
- * process exits; grids needing more (d * E^d * (N+1)^d values of the compute
- * type) return SEM_ERR_ARG.  The first call on a device looks the array up
- * with that device current, so make it before any stream capture.  All calls
- * share the array: calls whose kernels overlap on the GPU race and must be
- * ordered by the caller.  Arguments and errors otherwise as sem_rhs. */
+ * process exits; grids needing more (d * E^d * (N+1)^d values of 4 bytes in the
+ * FP32-bulk form, 8 otherwise) return SEM_ERR_ARG, and so do handles of
+ * sem_batch_create.  The first call on a device looks the array up with that
+ * device current, so make it before any stream capture.  All calls share the
+ * array: calls whose kernels overlap on the GPU race and must be ordered by the
+ * caller.  Arguments and errors otherwise as sem_rhs. */
 int sem_rhs_noalloc(sem_t h, const double* u, double* f, void* stream);
 
 /* Thread-local text of the last error ("" if none). */

@@ -66,6 +66,10 @@ extern "C" int sem_rhs_noalloc(sem_t h, const double* u, double* f, void* stream
         semk::set_error("sem_rhs_noalloc: null handle");
         return SEM_ERR_ARG;
     }
+    if (v.batch || !v.mats) {
+        semk::set_error("sem_rhs_noalloc: handles of sem_batch_create are not supported (use sem_rhs)");
+        return SEM_ERR_ARG;
+    }
     if (!u || !f || ((uintptr_t)u % 8) || ((uintptr_t)f % 8)) {
         semk::set_error("sem_rhs_noalloc: u and f must be non-null and 8-byte aligned");
         return SEM_ERR_ARG;
@@ -98,10 +102,22 @@ extern "C" int sem_rhs_noalloc(sem_t h, const double* u, double* f, void* stream
     a.nelem = v.nelem;
     a.plane = (unsigned)v.ndof;
     a.in_f2 = 0;
+    // the element kernel of the handle's precision, as sem_rhs runs it
     cudaError_t e;
-    if (v.dim == 1) e = v.fp32 ? semk::launch_elem<float, 1>(v.np, semk::OP_RHS, v.mats, a, s) : semk::launch_elem<double, 1>(v.np, semk::OP_RHS, v.mats, a, s);
-    else if (v.dim == 2) e = v.fp32 ? semk::launch_elem<float, 2>(v.np, semk::OP_RHS, v.mats, a, s) : semk::launch_elem<double, 2>(v.np, semk::OP_RHS, v.mats, a, s);
-    else e = v.fp32 ? semk::launch_elem<float, 3>(v.np, semk::OP_RHS, v.mats, a, s) : semk::launch_elem<double, 3>(v.np, semk::OP_RHS, v.mats, a, s);
+    const int op = semk::OP_RHS;
+    if (v.dfloat) {
+        if (v.dim == 1) e = semk::launch_elem<semk::dfloat, 1>(v.np, op, v.mats, a, s);
+        else if (v.dim == 2) e = semk::launch_elem<semk::dfloat, 2>(v.np, op, v.mats, a, s);
+        else e = semk::launch_elem<semk::dfloat, 3>(v.np, op, v.mats, a, s);
+    } else if (v.fp32) {
+        if (v.dim == 1) e = semk::launch_elem<float, 1>(v.np, op, v.mats, a, s);
+        else if (v.dim == 2) e = semk::launch_elem<float, 2>(v.np, op, v.mats, a, s);
+        else e = semk::launch_elem<float, 3>(v.np, op, v.mats, a, s);
+    } else {
+        if (v.dim == 1) e = semk::launch_elem<double, 1>(v.np, op, v.mats, a, s);
+        else if (v.dim == 2) e = semk::launch_elem<double, 2>(v.np, op, v.mats, a, s);
+        else e = semk::launch_elem<double, 3>(v.np, op, v.mats, a, s);
+    }
     if (e != cudaSuccess) {
         semk::set_error(cudaGetErrorString(e));
         return SEM_ERR_CUDA;

@@ -2142,7 +2142,9 @@ int semk::handle_view(sem_t h, HandleView* v) {
     v->ndof = h->ndof;
     v->lvec_elems = h->lvec_elems;
     v->fp32 = h->precision == SEM_PREC_FP32_BULK;
-    v->mats = h->mats.data();
+    v->dfloat = h->precision == SEM_PREC_FP64_DF;
+    v->batch = h->batch != nullptr;
+    v->mats = v->batch ? nullptr : h->mats.data();
     return SEM_OK;
 }
 

@@ -70,8 +70,10 @@ int objective_blocks(unsigned ndof);
 struct HandleView {
     int dim, E, N, G, np, nelem;
     size_t ndof, lvec_elems;
-    bool fp32;
-    const double* mats;   // 4 x np x np element matrices
+    bool fp32;            // SEM_PREC_FP32_BULK: FP32 element kernels and float element-local values
+    bool dfloat;          // SEM_PREC_FP64_DF: double-float element kernels, double element-local values
+    bool batch;           // a handle of sem_batch_create (packed instances; no single-grid tables)
+    const double* mats;   // 4 x np x np element matrices (null for batch handles)
 };
 int handle_view(struct ::sem_ctx* h, HandleView* v);
 void set_error(const char* msg);
