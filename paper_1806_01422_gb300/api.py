@@ -36,6 +36,8 @@ def _device(device):
 class Sem:
     """Periodic d-dimensional viscous Burgers on E^d GLL elements of order N (one GPU)."""
 
+    _fwd_token = 0     # counts forward sweeps run through this object (the handle keeps the last trajectory)
+
     def __init__(self, dim, E, N, nu, L_box=None, precision="fp64", ckpt="auto", ckpt_slots=0,
                  ckpt_budget_bytes=0, device=None):
         o = L.sem_opts(dim=dim, E=E, N=N, nu=float(nu), L=float(L_box or 0.0),
@@ -124,6 +126,7 @@ class Sem:
     def rk_forward(self, u0, dt, nsteps, scheme="rk4", out=None):
         u0 = self._dev(u0, "u0")
         out = self._out(out, "out")
+        self._fwd_token += 1           # the handle now keeps this sweep's trajectory
         L.check(L.lib().sem_rk_forward(self._h, SCHEMES[scheme], float(dt), int(nsteps), self._p(u0),
                                        self._p(out), _stream(self.device)))
         return out
@@ -147,6 +150,7 @@ class Sem:
         u0, u_obs = self._dev(u0, "u0"), self._dev(u_obs, "u_obs")
         grad = self._out(grad, "grad")
         J = ctypes.c_double()
+        self._fwd_token += 1
         L.check(L.lib().sem_objective_grad(self._h, SCHEMES[scheme], float(dt), int(nsteps), self._p(u0),
                                            self._p(u_obs), ctypes.byref(J), self._p(grad),
                                            _stream(self.device)))
@@ -298,17 +302,30 @@ def ckpt_plan(nsteps, slots):
 class SemMisfit(torch.autograd.Function):
     """u0 -> J(u0) = 1/2 ||u_N(u0) - u_obs||_M^2 with backward = the discrete adjoint sweep.
 
-    forward runs sem_objective_grad once (forward sweep, misfit, adjoint sweep) and
-    keeps the gradient; backward scales it by the incoming gradient.
+    forward runs the forward sweep (sem_rk_forward, which keeps the trajectory
+    the adjoint needs) and the misfit with its terminal adjoint M (u_N - u_obs);
+    backward runs the adjoint sweep (sem_rk_adjoint) from that terminal adjoint
+    and scales the gradient by the incoming gradient.  A forward-only use pays no
+    adjoint sweep.  If another forward sweep ran on the same handle in between
+    (the handle keeps only the last trajectory), backward repeats this one first.
     """
 
     @staticmethod
     def forward(ctx, u0, sem, u_obs, dt, nsteps, scheme):
-        J, g = sem.objective_grad(u0.detach(), u_obs, dt, nsteps, scheme)
-        ctx.save_for_backward(g)
+        u0d = u0.detach()
+        uN = sem.rk_forward(u0d, dt, nsteps, scheme)
+        lam = sem.empty()
+        J = sem.objective(uN, u_obs, lam)
+        ctx.sem, ctx.args, ctx.token = sem, (u0d, dt, nsteps, scheme), sem._fwd_token
+        ctx.save_for_backward(lam)
         return torch.tensor(J, dtype=torch.float64, device=u0.device)
 
     @staticmethod
     def backward(ctx, gJ):
-        (g,) = ctx.saved_tensors
+        (lam,) = ctx.saved_tensors
+        sem = ctx.sem
+        if sem._fwd_token != ctx.token:
+            u0d, dt, nsteps, scheme = ctx.args
+            sem.rk_forward(u0d, dt, nsteps, scheme)
+        g = sem.rk_adjoint(lam)
         return gJ * g, None, None, None, None, None

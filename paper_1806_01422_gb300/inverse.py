@@ -2,7 +2,7 @@
 
 Each L-BFGS iteration evaluates the misfit J(u0) = 1/2 ||u_N(u0) - u_obs||_M^2 and
 its gradient with one forward sweep and one discrete-adjoint sweep on the GPU
-(sem_objective_grad); the quasi-Newton update and the Moré-Thuente line
+(sem_objective_grad); the quasi-Newton update and the strong-Wolfe line
 search run on device tensors in FP64.
 """
 from . import _lib as L

@@ -1,13 +1,13 @@
-"""Limited-memory BFGS with a Moré-Thuente line search (the optimizer of Sec. 5.5).
+"""Limited-memory BFGS with a strong-Wolfe line search (the optimizer of Sec. 5.5).
 
 Sec. 5.5 of arXiv:1806.01422 drives the optimisation with TAO's LMVM method: a
 limited-memory quasi-Newton direction d_k = -H_k grad f(x_k) from the last m
-(s, y) pairs, then a Moré-Thuente line search for a step that satisfies the
-strong Wolfe conditions.  This module implements both from their published
-descriptions (Nocedal & Wright, Numerical Optimization, Alg. 7.4 two-loop
-recursion; Moré & Thuente, ACM TOMS 20 (1994), the safeguarded cubic/quadratic
-step on an interval of uncertainty).  Vectors are torch tensors (float64, on
-the GPU for the SEM problems); the objective callback returns (f, grad).
+(s, y) pairs, then a line search for a step that satisfies the strong Wolfe
+conditions (TAO's is More-Thuente's).  This module implements the two-loop
+recursion (Nocedal & Wright, Numerical Optimization, Alg. 7.4) and a
+bracket-and-zoom strong-Wolfe search (the same book, Alg. 3.5 and 3.6, with a
+safeguarded Hermite-cubic step).  Vectors are torch tensors (float64, on the GPU
+for the SEM problems); the objective callback returns (f, grad).
 """
 import math
 
@@ -18,146 +18,142 @@ def _dot(a, b):
     return float(torch.dot(a.reshape(-1), b.reshape(-1)))
 
 
-def _cstep(stx, fx, dx, sty, fy, dy, stp, fp, dp, brackt, stpmin, stpmax):
-    """One safeguarded step of the Moré-Thuente interval update.
+def _hermite_cubic_min(a, fa, da, b, fb, db):
+    """Minimiser of the cubic that matches f and f' at a and b (Nocedal & Wright eq. 3.59), or None."""
+    if a == b:
+        return None
+    d1 = da + db - 3.0 * (fa - fb) / (a - b)
+    disc = d1 * d1 - da * db
+    if not (disc >= 0.0) or not math.isfinite(disc):
+        return None
+    d2 = math.copysign(math.sqrt(disc), b - a)
+    den = db - da + 2.0 * d2
+    if den == 0.0:
+        return None
+    t = b - (b - a) * (db + d2 - d1) / den
+    return t if math.isfinite(t) else None
 
-    (stx, fx, dx): best step so far, (sty, fy, dy): other end of the interval,
-    (stp, fp, dp): trial step; f values and derivatives along the direction.
-    Returns the updated (stx, fx, dx, sty, fy, dy, new trial step, brackt).
+
+class LineSearchStalled(FloatingPointError):
+    """Every trial step was finite but none lowered f below f(0): f has stopped decreasing at
+    rounding level along the direction."""
+
+
+class _Probe:
+    """One evaluated trial step: t, phi(t), phi'(t) and the caller's payload."""
+    __slots__ = ("t", "f", "d", "payload")
+
+    def __init__(self, t, f, d, payload):
+        self.t, self.f, self.d, self.payload = t, f, d, payload
+
+    @property
+    def finite(self):
+        return math.isfinite(self.f) and math.isfinite(self.d)
+
+
+def wolfe_line_search(phi, f0, g0, t0=1.0, c1=1e-4, c2=0.9, maxfev=20, tmax=1e20):
+    """Step length satisfying the strong Wolfe conditions for phi(t) = f(x + t d).
+
+    The role of TAO's More-Thuente search in Sec. 5.5, written as the two-phase
+    method of Nocedal & Wright (Numerical Optimization, 2nd ed., Alg. 3.5 and
+    Alg. 3.6):
+
+    * bracketing: from t0 the step doubles until a trial either violates
+      sufficient decrease (or stops decreasing), or has a non-negative slope:
+      then [previous, trial] holds a step that satisfies both conditions;
+    * zoom: the bracket [lo, hi] shrinks around the minimiser of the cubic that
+      matches phi and phi' at both ends, kept at least a tenth of the bracket
+      away from either end (the midpoint when the cubic has no minimiser there);
+      lo is always the lowest point that satisfies sufficient decrease.
+
+    A trial whose value or slope is not finite (the model left its range of
+    validity) is a step that is too long: it becomes the far end of the bracket
+    and the search bisects towards lo.
+
+    phi(t) returns (f, slope along d, payload); f0, g0 are phi(0) and phi'(0) < 0.
+    Returns (t, f, payload, evaluations).  If no step satisfies both conditions
+    within maxfev evaluations, the lowest finite trial below f0 is returned; if
+    there is none, LineSearchStalled is raised when some trial was finite, and
+    FloatingPointError when none was.
     """
-    sgnd = dp * (dx / abs(dx)) if dx != 0.0 else dp
-    if fp > fx:
-        # higher function value: the minimiser is bracketed; cubic vs quadratic step
-        theta = 3.0 * (fx - fp) / (stp - stx) + dx + dp
-        s = max(abs(theta), abs(dx), abs(dp))
-        gamma = s * math.sqrt(max(0.0, (theta / s) ** 2 - (dx / s) * (dp / s)))
-        if stp < stx:
-            gamma = -gamma
-        p = (gamma - dx) + theta
-        q = ((gamma - dx) + gamma) + dp
-        stpc = stx + (p / q) * (stp - stx)
-        stpq = stx + ((dx / ((fx - fp) / (stp - stx) + dx)) / 2.0) * (stp - stx)
-        stpf = stpc if abs(stpc - stx) < abs(stpq - stx) else stpc + (stpq - stpc) / 2.0
-        brackt = True
-    elif sgnd < 0.0:
-        # derivatives of opposite sign: bracketed
-        theta = 3.0 * (fx - fp) / (stp - stx) + dx + dp
-        s = max(abs(theta), abs(dx), abs(dp))
-        gamma = s * math.sqrt(max(0.0, (theta / s) ** 2 - (dx / s) * (dp / s)))
-        if stp > stx:
-            gamma = -gamma
-        p = (gamma - dp) + theta
-        q = ((gamma - dp) + gamma) + dx
-        stpc = stp + (p / q) * (stx - stp)
-        stpq = stp + (dp / (dp - dx)) * (stx - stp)
-        stpf = stpc if abs(stpc - stp) > abs(stpq - stp) else stpq
-        brackt = True
-    elif abs(dp) < abs(dx):
-        # same sign, derivative magnitude decreases
-        theta = 3.0 * (fx - fp) / (stp - stx) + dx + dp
-        s = max(abs(theta), abs(dx), abs(dp))
-        gamma = s * math.sqrt(max(0.0, (theta / s) ** 2 - (dx / s) * (dp / s)))
-        if stp > stx:
-            gamma = -gamma
-        p = (gamma - dp) + theta
-        q = (gamma + (dx - dp)) + gamma
-        r = p / q
-        stpc = stp + r * (stx - stp) if (r < 0.0 and gamma != 0.0) else (stpmax if stp > stx else stpmin)
-        stpq = stp + (dp / (dp - dx)) * (stx - stp)
-        if brackt:
-            stpf = stpc if abs(stpc - stp) < abs(stpq - stp) else stpq
-            stpf = min(stp + 0.66 * (sty - stp), stpf) if stp > stx else max(stp + 0.66 * (sty - stp), stpf)
-        else:
-            stpf = stpc if abs(stpc - stp) > abs(stpq - stp) else stpq
-            stpf = min(stpmax, max(stpmin, stpf))
-    else:
-        # same sign, derivative magnitude does not decrease
-        if brackt:
-            theta = 3.0 * (fp - fy) / (sty - stp) + dy + dp
-            s = max(abs(theta), abs(dy), abs(dp))
-            gamma = s * math.sqrt(max(0.0, (theta / s) ** 2 - (dy / s) * (dp / s)))
-            if stp > sty:
-                gamma = -gamma
-            p = (gamma - dp) + theta
-            q = ((gamma - dp) + gamma) + dy
-            stpf = stp + (p / q) * (sty - stp)
-        else:
-            stpf = stpmax if stp > stx else stpmin
-    # update the interval of uncertainty
-    if fp > fx:
-        sty, fy, dy = stp, fp, dp
-    else:
-        if sgnd < 0.0:
-            sty, fy, dy = stx, fx, dx
-        stx, fx, dx = stp, fp, dp
-    return stx, fx, dx, sty, fy, dy, stpf, brackt
-
-
-def more_thuente(phi, f0, g0, stp=1.0, ftol=1e-4, gtol=0.9, xtol=1e-10, stpmin=1e-20, stpmax=1e20, maxfev=20):
-    """Step satisfying the strong Wolfe conditions for phi(t) = f(x + t d).
-
-    phi(t) returns (f, derivative along d, payload); f0, g0 at t = 0 (g0 < 0).
-    A trial step whose f or derivative is not finite (the model left its range of
-    validity) becomes the new upper limit of the step and the next trial moves
-    halfway back towards the best step so far.
-    Returns (t, f, payload, evaluations).
-    """
-    if g0 >= 0.0:
+    if not g0 < 0.0:
         raise ValueError("not a descent direction")
-    brackt, stage1 = False, True
-    gtest = ftol * g0
-    width, width1 = stpmax - stpmin, 2.0 * (stpmax - stpmin)
-    stx, fx, gx = 0.0, f0, g0
-    sty, fy, gy = 0.0, f0, g0
-    best = None
-    for nfev in range(1, maxfev + 1):
-        if brackt:
-            stmin, stmax = min(stx, sty), max(stx, sty)
-        else:
-            stmin, stmax = stx, stp + 4.0 * (stp - stx)
-        stp = min(max(stp, stpmin), stpmax)
-        if brackt and (stp <= stmin or stp >= stmax or stmax - stmin <= xtol * stmax):
-            stp = stx
-        f, g, payload = phi(stp)
-        if not (math.isfinite(f) and math.isfinite(g)):
-            stpmax = stp
-            stp = stx + 0.5 * (stp - stx)
-            continue
-        if best is None or f < best[1]:
-            best = (stp, f, payload)
-        ftest = f0 + stp * gtest
-        if f <= ftest and abs(g) <= gtol * (-g0):
-            return stp, f, payload, nfev          # strong Wolfe conditions hold
-        if brackt and stmax - stmin <= xtol * stmax:
+    nfev = 0
+    best = None                      # lowest finite trial with f < f0
+    any_finite = False
+
+    def probe(t):
+        nonlocal nfev, best, any_finite
+        f, d, payload = phi(t)
+        nfev += 1
+        p = _Probe(t, f, d, payload)
+        any_finite = any_finite or p.finite
+        if p.finite and f < f0 and (best is None or f < best.f):
+            best = p
+        return p
+
+    def armijo(p):
+        return p.finite and p.f <= f0 + c1 * p.t * g0
+
+    def curvature(p):
+        return abs(p.d) <= c2 * abs(g0)
+
+    def zoom(lo, hi):
+        while nfev < maxfev:
+            w = hi.t - lo.t
+            t = None
+            if hi.finite:
+                t = _hermite_cubic_min(lo.t, lo.f, lo.d, hi.t, hi.f, hi.d)
+            left, right = min(lo.t, hi.t) + 0.1 * abs(w), max(lo.t, hi.t) - 0.1 * abs(w)
+            if t is None or not (left <= t <= right):
+                t = lo.t + 0.5 * w
+            if t == lo.t or t == hi.t:
+                break
+            p = probe(t)
+            if not armijo(p) or p.f >= lo.f:
+                hi = p
+                continue
+            if curvature(p):
+                return p
+            if p.d * (hi.t - lo.t) >= 0.0:
+                hi = lo
+            lo = p
+        return None
+
+    prev = _Probe(0.0, f0, g0, None)
+    t = min(t0, tmax)
+    found = None
+    while nfev < maxfev:
+        p = probe(t)
+        if not armijo(p) or (prev.t > 0.0 and p.f >= prev.f):
+            found = zoom(prev, p)
             break
-        if stage1 and f <= ftest and g >= min(ftol, gtol) * g0:
-            stage1 = False
-        if stage1 and f <= fx and f > ftest:
-            # modified function psi(t) = phi(t) - t gtest in the first stage
-            fm, fxm, fym = f - stp * gtest, fx - stx * gtest, fy - sty * gtest
-            gm, gxm, gym = g - gtest, gx - gtest, gy - gtest
-            stx, fxm, gxm, sty, fym, gym, stp, brackt = _cstep(stx, fxm, gxm, sty, fym, gym, stp, fm, gm, brackt,
-                                                               stmin, stmax)
-            fx, fy = fxm + stx * gtest, fym + sty * gtest
-            gx, gy = gxm + gtest, gym + gtest
-        else:
-            stx, fx, gx, sty, fy, gy, stp, brackt = _cstep(stx, fx, gx, sty, fy, gy, stp, f, g, brackt,
-                                                           stmin, stmax)
-        if brackt:
-            if abs(sty - stx) >= 0.66 * width1:
-                stp = stx + 0.5 * (sty - stx)
-            width1, width = width, abs(sty - stx)
-    if best is None:
+        if curvature(p):
+            found = p
+            break
+        if p.d >= 0.0:
+            found = zoom(p, prev)
+            break
+        if t >= tmax:
+            found = p
+            break
+        prev, t = p, min(2.0 * t, tmax)
+    if found is None:
+        found = best
+    if found is None and any_finite:
+        raise LineSearchStalled("no trial step lowered f below f(0) along the search direction")
+    if found is None:
         raise FloatingPointError("no finite function value along the search direction")
-    return best[0], best[1], best[2], maxfev
+    return found.t, found.f, found.payload, nfev
 
 
 def lbfgs(fg, x0, m=8, max_iter=30, gtol=1e-8, callback=None, line_search_maxfev=20, h0_diag=None):
-    """Minimise f with L-BFGS (two-loop recursion) and the Moré-Thuente line search.
+    """Minimise f with L-BFGS (two-loop recursion) and the strong-Wolfe line search.
 
     fg(x) -> (f, grad); x0: tensor.  Returns (x, history) where history holds
     (iteration, f, |grad|, function evaluations).  Stops after max_iter
-    iterations or when |grad| <= gtol |grad_0|.
+    iterations, when |grad| <= gtol |grad_0|, or when no step along the
+    quasi-Newton direction lowers f any more (rounding level).
 
     h0_diag: optional diagonal of the initial inverse Hessian H_0 (a tensor like x).
     Without it H_0 = gamma I (Nocedal & Wright eq. 7.20) and the first step is a unit
@@ -206,7 +202,10 @@ def lbfgs(fg, x0, m=8, max_iter=30, gtol=1e-8, callback=None, line_search_maxfev
             gt = gt.clone()
             return ft, _dot(gt, d), (xt, gt)
 
-        t, fn, (xn, gn), ne = more_thuente(phi, f, dg, stp=1.0, maxfev=line_search_maxfev)
+        try:
+            t, fn, (xn, gn), ne = wolfe_line_search(phi, f, dg, t0=1.0, maxfev=line_search_maxfev)
+        except LineSearchStalled:
+            break                   # f no longer decreases above rounding: x is as good as it gets
         nfev += ne
         s, y = xn - x, gn - g
         sy = _dot(s, y)

@@ -196,6 +196,24 @@ def test_autograd_function_gradient():
     assert relerr(u0.grad, lam_ref) < RTOL64
 
 
+def test_autograd_function_forward_runs_no_adjoint_and_survives_an_intervening_forward():
+    s, g = pair(2, 4, 5, nu=0.01)
+    u0a = torch.from_numpy(smooth(g, 1)).cuda().requires_grad_(True)
+    u0b = torch.from_numpy(smooth(g, 3)).cuda().requires_grad_(True)
+    uo = torch.from_numpy(smooth(g, 2)).cuda()
+    Ja = SemMisfit.apply(u0a, s, uo, 2e-4, 10, "rk4")
+    torch.cuda.synchronize()
+    assert s.sweep_stats()["adjoint_jacT"] == 0          # forward only: no adjoint sweep yet
+    Jb = SemMisfit.apply(u0b, s, uo, 2e-4, 10, "rk4")   # overwrites the handle's trajectory
+    Ja.backward()
+    Jref, gref = s.objective_grad(u0a.detach(), uo, 2e-4, 10, "rk4")
+    assert float(Ja) == Jref
+    assert torch.equal(u0a.grad, gref)
+    Jb.backward()
+    _, gref_b = s.objective_grad(u0b.detach(), uo, 2e-4, 10, "rk4")
+    assert torch.equal(u0b.grad, gref_b)
+
+
 def test_host_buffers_give_the_same_result():
     s, g = pair(2, 4, 7)
     u0 = torch.from_numpy(smooth(g, 1)).pin_memory()

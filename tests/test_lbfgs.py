@@ -1,18 +1,18 @@
-"""L-BFGS with the Moré-Thuente line search on problems with known minimisers (CPU)."""
+"""L-BFGS with the strong-Wolfe line search on problems with known minimisers (CPU)."""
 import math
 
 import numpy as np
 import pytest
 import torch
 
-from paper_1806_01422_gb300.lbfgs import lbfgs, more_thuente
+from paper_1806_01422_gb300.lbfgs import lbfgs, wolfe_line_search
 
 
 def test_line_search_satisfies_strong_wolfe_on_a_quartic():
     # phi(t) = (t - 2)^4 - t: minimiser where 4 (t - 2)^3 = 1
     phi = lambda t: ((t - 2) ** 4 - t, 4 * (t - 2) ** 3 - 1, None)
     f0, g0, _ = phi(0.0)
-    t, f, _, n = more_thuente(phi, f0, g0, stp=1.0, ftol=1e-4, gtol=0.1)
+    t, f, _, n = wolfe_line_search(phi, f0, g0, t0=1.0, c1=1e-4, c2=0.1)
     assert f <= f0 + 1e-4 * t * g0
     assert abs(phi(t)[1]) <= 0.1 * abs(g0)
 
@@ -44,7 +44,7 @@ def test_line_search_backs_off_from_non_finite_values():
         if t >= 0.3:
             return math.inf, math.nan, None
         return (t - 0.2) ** 2, 2.0 * (t - 0.2), t
-    t, f, payload, nfev = more_thuente(phi, 0.04, -0.4, stp=1.0)
+    t, f, payload, nfev = wolfe_line_search(phi, 0.04, -0.4, t0=1.0)
     assert t < 0.3 and f < 0.04 and payload == t
 
 
@@ -58,3 +58,25 @@ def test_diagonal_initial_hessian_solves_a_badly_scaled_quadratic_at_once():
     assert hist[1][1] < 1e-28 and float(x.abs().max()) < 1e-14
     _, plain = lbfgs(fg, x0, max_iter=3)
     assert plain[-1][1] > 1e-6          # the unscaled method is still far off after 3 iterations
+
+
+@pytest.mark.parametrize("tmin", [0.01, 0.3, 0.9, 1.7, 7.0, 60.0])
+@pytest.mark.parametrize("c2", [0.9, 0.1])
+def test_line_search_zoom_and_expansion_meet_strong_wolfe(tmin, c2):
+    """phi(t) = exp-shaped valley with its minimiser at tmin: the unit step overshoots (zoom) or
+    undershoots (expansion); either way the returned step satisfies both strong Wolfe conditions."""
+    def phi(t):
+        z = t / tmin
+        return z * z - 2.0 * math.log1p(z * z) * 0.25 - 2.0 * z, (2 * z - z / (1 + z * z) - 2.0) / tmin, None
+    f0, g0, _ = phi(0.0)
+    t, f, _, n = wolfe_line_search(phi, f0, g0, t0=1.0, c1=1e-4, c2=c2, maxfev=40)
+    assert f <= f0 + 1e-4 * t * g0
+    assert abs(phi(t)[1]) <= c2 * abs(g0) * (1 + 1e-12)
+    assert n <= 40
+
+
+def test_line_search_returns_best_decrease_when_budget_runs_out():
+    """With one evaluation allowed the search returns the decreasing trial it has."""
+    phi = lambda t: ((t - 3.0) ** 2 - 9.0, 2.0 * (t - 3.0), "p%g" % t)
+    t, f, payload, n = wolfe_line_search(phi, 0.0, -6.0, t0=1.0, maxfev=1)
+    assert n == 1 and t == 1.0 and f == -5.0 and payload == "p1"
