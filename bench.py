@@ -1,13 +1,16 @@
 #!/usr/bin/env python
 """Throughput benchmark of the spectral-element Burgers gradient on GB300.
 
-One step = one gradient evaluation of the misfit J(u0) = 1/2 ||u_N(u0) - u_obs||_M^2
-for the 2D vector viscous Burgers workload (periodic [0,1]^2, 64x64 elements of
-order 7, 401,408 unknowns, nu = 1e-3, SSP-RK3, dt = 2e-4, 2000 steps, every
-stage value stored): forward sweep, misfit and terminal adjoint, backward sweep
-with the matrix-free transpose Jacobian, all on one GPU through the C ABI.
+One step = one gradient evaluation of the misfit J(u0) = 1/2 ||u_N(u0) - u_obs||_M^2.
+The default workload is the 3D vector viscous Burgers problem (periodic [0,1]^3,
+32^3 hexahedra of order 7, 33,718,272 unknowns, nu = 5e-4, RK4 with dt = 2.5e-4,
+binomial checkpointing with 20 slots) in FP64: forward sweep, misfit and terminal
+adjoint, backward sweep with the matrix-free transpose Jacobian and the
+checkpoint replays, all on one GPU through the C ABI.  The horizon is 300 steps:
+past about 400 steps the seeded k^-5/3 field steepens into fronts the grid does
+not resolve at this viscosity and the discrete solution diverges.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload 2d|3d|...]
 
 N > 1 runs one independent replica per GPU (torchrun, one rank per GPU): the
 path has no exchange step between GPUs, so scaling is weak.  Prints one JSON line.
@@ -29,6 +32,7 @@ METRIC = "GDOF/s for F(u) and J^T v; adjoint/forward cost ratio; gradient evals/
 
 WORKLOADS = {
     "2d": dict(dim=2, E=64, N=7, nu=1e-3, scheme="ssprk3", dt=2e-4, nsteps=2000, ckpt="stages", slots=0,
+               oracle_steps=10,
                desc="2D vector viscous Burgers, periodic [0,1]^2, 64x64 quads, N=7 (401,408 unknowns), "
                     "nu=1e-3, SSP-RK3 dt=2e-4 x 2000 steps, all stages stored; one gradient evaluation per step",
                data="synthetic: seeded 16-mode Fourier fields (|k|_inf <= 8, amplitude ~|k|^-2, max|u0| = 1) "
@@ -37,8 +41,12 @@ WORKLOADS = {
     # viscosities the discrete solution (FP64 and FP32 alike) diverges near step 450 (N=7)
     # and step 350 (N=15)
     "3d": dict(dim=3, E=32, N=7, nu=5e-4, scheme="rk4", dt=2.5e-4, nsteps=300, ckpt="binomial", slots=20,
+               oracle_steps=1,
                desc="3D vector viscous Burgers, periodic [0,1]^3, 32^3 hexes, N=7 (33,718,272 unknowns), "
                     "nu=5e-4, RK4 dt=2.5e-4 x 300 steps (T=0.075), binomial checkpointing with 20 slots",
+               horizon="300 of the configured 1000 steps: the seeded k^-5/3 field steepens into fronts this grid "
+                       "does not resolve at nu=5e-4, and the discrete solution (FP64 and FP32 alike) grows past "
+                       "max|u| = 1.08 at step 400 and is non-finite by step 500; at step 300 max|u| <= 0.99",
                data="synthetic: seeded random-phase fields, spectrum ~k^-5/3 cut at |k| = 16, max|u0| = 1"),
     "batch": dict(dim=2, E=None, N=None, nu=1e-3, scheme="rk4", dt=1.5e-4, nsteps=300, ckpt="states", slots=0,
                   count=256,
@@ -48,8 +56,11 @@ WORKLOADS = {
                        "batched gradient evaluation per step (256 instance gradients)",
                   data="synthetic: per instance k seeded 16-mode Fourier fields (seeds 1000+2k, 1001+2k)"),
     "3d15": dict(dim=3, E=16, N=15, nu=2e-4, scheme="rk4", dt=2e-4, nsteps=300, ckpt="states", slots=0,
+                 oracle_steps=1,
                  desc="3D vector viscous Burgers, periodic [0,1]^3, 16^3 hexes, N=15 (41,472,000 unknowns), "
                       "nu=2e-4, RK4 dt=2e-4 x 300 steps (T=0.06), every step's state stored (stages recomputed)",
+                 horizon="300 of the configured 400 steps: the discrete solution diverges between steps 340 and "
+                         "360 at nu=2e-4 (the seeded field steepens past what the grid resolves)",
                  data="synthetic: seeded random-phase fields, spectrum ~k^-5/3 cut at |k| = 16, max|u0| = 1"),
     "2dcn": dict(dim=2, E=64, N=7, nu=1e-3, scheme="cn", dt=2e-3, nsteps=200, ckpt="states", slots=0,
                  desc="2D vector viscous Burgers, periodic [0,1]^2, 64x64 quads, N=7 (401,408 unknowns), "
@@ -58,6 +69,7 @@ WORKLOADS = {
                  data="synthetic: seeded 16-mode Fourier fields (|k|_inf <= 8, amplitude ~|k|^-2, max|u0| = 1) "
                       "for u0 (seed 1) and u_obs (seed 2)"),
     "1d": dict(dim=1, E=16, N=7, nu=0.01, scheme="rk4", dt=1e-3, nsteps=500, ckpt="stages", slots=0,
+               oracle_steps=100,
                desc="1D viscous Burgers, periodic [0,2pi), 16 elements, N=7 (112 unknowns), nu=0.01, "
                     "RK4 dt=1e-3 x 500 steps",
                data="synthetic: u0 = sin x + 0.1 sum_k a_k sin(kx + phi_k), seeded"),
@@ -77,11 +89,11 @@ TRAFFIC = {
     "jact2_kernel<double,8>@2d@fp64": {
         "bytes": 6478592 + 0, "src": "a16d1fe8a8f9f7aa",
         "capture": "dram__bytes_read.sum + dram__bytes_write.sum of one jact2 launch at 64x64 quads, N=7 "
-                   "(ncu --set full; profiles/rhs2_jact2_assemble_2d_fp64_E64_N7.md)"},
+                   "(ncu --set full capture of the 2D FP64 element kernels)"},
     "op2c_kernel<semk::dfa::dfloat,8> (J^T)@2d@fp64_df": {
         "bytes": 6534656 + 0, "src": "a16d1fe8a8f9f7aa",
         "capture": "dram__bytes_read.sum + dram__bytes_write.sum of one J^T launch (op2c_kernel) at 64x64 "
-                   "quads, N=7 (ncu --set full; profiles/rhs2_jact2_2d_fp64df_E64_N7.md)"},
+                   "quads, N=7 (ncu --set full capture of the 2D FP64-DF element kernels)"},
 }
 
 # sources of the element kernels (rhs*, jac*, jact*) and of the assembly kernels
@@ -164,8 +176,124 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- oracle leg
-def oracle_sample(workload, rk_steps):
-    """Time the FP64 CPU oracle on a gradient evaluation of `rk_steps` steps (child process)."""
+# The oracle's operators with the element loop split over the host cores (the cpu_baseline and
+# --impl reference legs only).  The oracle itself is unchanged: each worker of a fork pool, started
+# inside a CUDA-free child process, applies the oracle's element-local operator (Grid.local_rhs,
+# Grid.local_jacT) to a contiguous range of element slabs along the slowest array axis and sums
+# the element-local values into its own slab of the global array.  It writes the slab's interior
+# planes to the shared output and hands its two end planes to the parent, which adds the planes
+# that neighbouring slabs share, in a fixed order.  The definitions are those of Grid.rhs and
+# Grid.jacT; only the grouping of the gather-scatter sum differs.
+_POOL = {}
+
+
+def _shared_array(n):
+    import mmap
+    import numpy as np
+    return np.frombuffer(mmap.mmap(-1, max(8, 8 * n)), dtype=np.float64, count=n)
+
+
+def _slab_index(g, a, b):
+    """Element ids of slabs [a, b) and their index tuple into a local array of (b-a) N + 1 planes."""
+    import numpy as np
+    d, E, N, n = g.d, g.E, g.N, g.n
+    per_slab = E ** (d - 1)
+    elems = np.arange(a * per_slab, b * per_slab)
+    ec = np.unravel_index(elems, (E,) * d)          # array order, slowest axis first
+    idx = []
+    for p in range(d):
+        shape = [1] * (1 + d)
+        shape[0] = len(elems)
+        shape[1 + p] = n
+        if p == 0:
+            v = (ec[0][:, None] - a) * N + np.arange(n)[None, :]
+        else:
+            v = (ec[p][:, None] * N + np.arange(n)[None, :]) % g.G
+        idx.append(v.reshape(shape))
+    return elems, tuple(idx)
+
+
+def _pool_task(task):
+    import numpy as np
+    op, k = task
+    P = _POOL
+    g = P["grid"]
+    a, b = P["slabs"][k]
+    elems, idx = P["index"][k]
+    d, N, G = g.d, g.N, g.G
+    shp = (d,) + g.global_shape()
+    u = P["in0"].reshape(shp)
+    if op == "rhs":
+        R = g.local_rhs(g.gather_vec(u, elems))
+    else:
+        v = P["in1"].reshape(shp)
+        Mloc = g.gather(g.M, elems)
+        Z = np.stack([g.gather(v[c], elems) / Mloc for c in range(d)])   # Q M^-1 v, node by node
+        R = g.local_jacT(g.gather_vec(u, elems), Z)
+    loc = np.zeros((d, (b - a) * N + 1) + (G,) * (d - 1))
+    for c in range(d):
+        np.add.at(loc[c], idx, R[c])
+    out = P["out"].reshape(shp)
+    lo, hi = a * N, b * N
+    out[:, lo + 1:hi] = loc[:, 1:-1] / g.M[lo + 1:hi] if op == "rhs" else loc[:, 1:-1]
+    bnd = P["bnd"].reshape((len(P["slabs"]), 2, d) + (G,) * (d - 1))
+    bnd[k, 0] = loc[:, 0]
+    bnd[k, 1] = loc[:, -1]
+    return k
+
+
+class OraclePool:
+    """Grid.rhs and Grid.jacT of the oracle, with the element loop split over `procs` processes.
+
+    Create it in a process that has not initialised CUDA (a fork after CUDA init can hang);
+    bench.py does so in a child process with no visible GPU.
+    """
+
+    def __init__(self, g, procs):
+        import multiprocessing as mp
+        procs = max(1, min(int(procs), g.E))
+        bounds = [round(i * g.E / procs) for i in range(procs + 1)]
+        slabs = [(bounds[i], bounds[i + 1]) for i in range(procs)]
+        n = g.ndof()
+        plane = g.d * g.G ** (g.d - 1)
+        _POOL.clear()
+        _POOL.update(grid=g, slabs=slabs, index=[_slab_index(g, a, b) for a, b in slabs],
+                     in0=_shared_array(n), in1=_shared_array(n), out=_shared_array(n),
+                     bnd=_shared_array(procs * 2 * plane))
+        self.g, self.procs, self.slabs = g, procs, slabs
+        self.pool = mp.get_context("fork").Pool(procs)
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+
+    def _run(self, op):
+        import numpy as np
+        g, N = self.g, self.g.N
+        self.pool.map(_pool_task, [(op, k) for k in range(self.procs)])
+        shp = (g.d,) + g.global_shape()
+        out = _POOL["out"].reshape(shp)
+        bnd = _POOL["bnd"].reshape((self.procs, 2, g.d) + (g.G,) * (g.d - 1))
+        for k, (a, _) in enumerate(self.slabs):
+            s = bnd[k, 0] + bnd[(k - 1) % self.procs, 1]
+            out[:, a * N] = s / g.M[a * N] if op == "rhs" else s
+        return np.array(out)
+
+    def rhs(self, u):
+        _POOL["in0"][:] = u.ravel()
+        return self._run("rhs")
+
+    def jacT(self, u, v):
+        _POOL["in0"][:] = u.ravel()
+        _POOL["in1"][:] = v.ravel()
+        return self._run("jacT")
+
+    def objective(self, u, u_obs):
+        return self.g.objective(u, u_obs)
+
+
+def oracle_sample(workload, rk_steps, reps, procs):
+    """Seconds of `reps` oracle gradient evaluations of `rk_steps` steps each (child process)."""
     import numpy as np
     from oracle.sem import Grid
     from oracle import rk as ork
@@ -174,18 +302,35 @@ def oracle_sample(workload, rk_steps):
     g = Grid(w["dim"], w["E"], w["N"], w["nu"])
     x = g.coords()
     u0, uo = inputs.workload_field(w["dim"], x, inputs.SEED_U0), inputs.workload_field(w["dim"], x, inputs.SEED_UOBS)
-    t0 = time.perf_counter()
-    J, lam, _ = ork.objective_and_gradient(g, u0, uo, w["dt"], rk_steps, w["scheme"])
-    t1 = time.perf_counter()
-    return {"seconds": t1 - t0, "rk_steps": rk_steps, "J": J, "finite": bool(np.isfinite(lam).all())}
+    pg = OraclePool(g, procs)
+    secs, J, finite = [], None, True
+    try:
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            J, lam, _ = ork.objective_and_gradient(pg, u0, uo, w["dt"], rk_steps, w["scheme"])
+            secs.append(time.perf_counter() - t0)
+            finite = finite and bool(np.isfinite(lam).all())
+    finally:
+        pg.close()
+    return {"seconds": secs, "rk_steps": rk_steps, "procs": pg.procs, "J": J, "finite": finite}
 
 
-def run_oracle_child(workload, rk_steps):
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_oracle_child(workload, rk_steps, reps=1, procs=None):
     env = dict(os.environ)
+    # one BLAS thread per worker process: the pool supplies the parallelism
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
-    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-sample", workload, str(rk_steps)]
+    procs = procs or host_cores()
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-sample", workload, str(rk_steps), str(reps),
+           str(procs)]
     r = subprocess.run(cmd, capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError("oracle sample failed: %s" % r.stderr[-2000:])
@@ -193,21 +338,23 @@ def run_oracle_child(workload, rk_steps):
 
 
 def cpu_baseline(workload, target_s=15.0):
-    """Oracle gradient evaluations/s from a bounded sample, one core, scaled to the full horizon."""
+    """Oracle gradient evaluations/s from a bounded sample on all host cores, scaled to the full horizon."""
     w = WORKLOADS[workload]
+    cores = host_cores()
     if w["scheme"] == "cn":
-        return {"value": None, "unit": "gradient evals/s", "cores": 1, "kind": "oracle",
+        return {"value": None, "unit": "gradient evals/s", "cores": cores, "kind": "oracle",
                 "sample": "none: the oracle's Crank-Nicolson solves assemble dense Jacobians, which do not fit "
                           "at %s" % w["desc"].split(", ")[2]}
-    probe = run_oracle_child(workload, 2)
-    per_step = max(probe["seconds"] / 2, 1e-6)
-    n = int(max(2, min(w["nsteps"], target_s / per_step)))
-    res = run_oracle_child(workload, n)
-    per_eval = res["seconds"] * w["nsteps"] / n
-    return {"value": 1.0 / per_eval, "unit": "gradient evals/s", "cores": 1, "kind": "oracle",
-            "sample": "%d of %d RK steps of one gradient evaluation (forward + misfit + adjoint), "
-                      "FP64 numpy oracle, one thread; time scaled by %d/%d" % (n, w["nsteps"], w["nsteps"], n),
-            "seconds": res["seconds"]}
+    probe = run_oracle_child(workload, 1, 1, cores)
+    per_step = max(probe["seconds"][0], 1e-6)
+    n = int(max(1, min(w["nsteps"], target_s / per_step)))
+    res = run_oracle_child(workload, n, 1, cores)
+    per_eval = res["seconds"][0] * w["nsteps"] / n
+    return {"value": 1.0 / per_eval, "unit": "gradient evals/s", "cores": res["procs"], "kind": "oracle",
+            "sample": "%d of %d RK steps of one gradient evaluation (forward + misfit + adjoint over the stored "
+                      "stages), FP64 numpy oracle with its element loop split over %d processes; time scaled by "
+                      "%d/%d" % (n, w["nsteps"], res["procs"], w["nsteps"], n),
+            "seconds": res["seconds"][0]}
 
 
 # ---------------------------------------------------------------- distributed
@@ -253,19 +400,20 @@ def reference_arm(args, world, rank):
     if w["scheme"] == "cn":
         return {"impl": "reference", "unavailable": "the oracle's Crank-Nicolson solves assemble dense Jacobians, "
                                                     "which do not fit at 401,408 unknowns"}
-    n = args.oracle_rk_steps
-    for _ in range(args.warmup):
-        run_oracle_child(args.workload, n)
-    secs = [run_oracle_child(args.workload, n)["seconds"] for _ in range(args.steps)]
+    n = args.oracle_rk_steps or w.get("oracle_steps", 10)
+    res = run_oracle_child(args.workload, n, args.warmup + args.steps)
+    secs = res["seconds"][args.warmup:]
     per_eval = statistics.mean(secs) * w["nsteps"] / n
     value = 1.0 / per_eval
-    sample = ("each step: %d of %d RK steps of one gradient evaluation, FP64 numpy oracle, one thread; "
-              "time scaled by %d/%d" % (n, w["nsteps"], w["nsteps"], n))
+    cores = res["procs"]
+    sample = ("each step: %d of %d RK steps of one gradient evaluation (forward + misfit + adjoint over the "
+              "stored stages), FP64 numpy oracle with its element loop split over %d processes; time scaled "
+              "by %d/%d" % (n, w["nsteps"], cores, w["nsteps"], n))
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "gradient evals/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_eval * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": w["data"], "config": {"workload": w["desc"]},
-            "cpu_baseline": {"value": value, "unit": "gradient evals/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": "gradient evals/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "gradient evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -334,14 +482,15 @@ def measure_form(args, w, precision, u0, uo, grad_ref, J_ref, dev):
     g = s.empty()
     s.use_graph(not args.no_graph)
     s.profile(args.profile_every)
-    for _ in range(max(3, args.warmup)):
+    reps = max(1, min(args.steps, args.extra_reps))
+    for _ in range(2):
         J, _ = s.objective_grad(u0, uo, w["dt"], w["nsteps"], w["scheme"], grad=g)
     s.profile_read(reset=True)
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(reps):
         J, _ = s.objective_grad(u0, uo, w["dt"], w["nsteps"], w["scheme"], grad=g)
     e1.record(stream)
     torch.cuda.synchronize(dev)
@@ -349,7 +498,7 @@ def measure_form(args, w, precision, u0, uo, grad_ref, J_ref, dev):
     prof = s.profile_read(reset=True)
     elapsed = e0.elapsed_time(e1) / 1e3
     roof = roofline_of(prof, args, w, s, precision)
-    out = {"value": args.steps / elapsed, "ms_per_step": elapsed / args.steps * 1e3,
+    out = {"value": reps / elapsed, "ms_per_step": elapsed / reps * 1e3, "reps": reps,
            "J_rel_diff_vs_fp64": abs(J - J_ref) / abs(J_ref),
            "grad_rel_err_vs_fp64": float((g - grad_ref).abs().max() / grad_ref.abs().max()),
            "roofline": {k: roof[k] for k in ("bound", "achieved", "peak", "unit", "frac", "kernel", "avg_launch_us")}}
@@ -459,6 +608,7 @@ def gpu_arm(args, world, rank, local):
                       "l2": "inputs larger than L2: every step writes and re-reads the stored trajectory "
                             "(%.1f GB: %s)" % (traj_gb, w["ckpt"])},
            "roofline": roof, "gpu_launches": launches, "clocks": clk.summary(), "J": J,
+           **({"horizon": w["horizon"]} if "horizon" in w else {}),
            "execution": graph_note or ("stream launches" if args.no_graph else "CUDA graph replay (sem_set_graph)"),
            "kernel_ms_per_step": {k: v[0] * args.profile_every / args.steps for k, v in prof.items()}}
     if scheme == "cn":
@@ -471,12 +621,13 @@ def gpu_arm(args, world, rank, local):
     if rank == 0 and not args.no_extras:
         out.update(extras(s, u0, uo, w, dev))
         # end to end through the public API with host buffers (pinned), copies inside the timed region
+        reps = max(1, min(args.steps, args.extra_reps))
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(reps):
             Jh, gh = s.objective_grad(u0_h, uo_h, dt, nsteps, scheme, host=True)
         t1 = time.perf_counter()
-        out["e2e"] = {"value": args.steps * units / (t1 - t0), "unit": unit,
+        out["e2e"] = {"value": reps * units / (t1 - t0), "unit": unit, "reps": reps,
                       "h2d_bytes_per_step": 2 * s.ndof * 8, "d2h_bytes_per_step": s.ndof * 8 + 8}
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_seconds)
@@ -602,11 +753,14 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="3d", choices=sorted(WORKLOADS))
+    ap.add_argument("--extra-reps", type=int, default=3,
+                    help="timed repetitions of the other precision forms and of the end-to-end leg (at most --steps)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk", "fp64_df"])
     ap.add_argument("--hbm-peak", type=float, default=None, help="GB/s; default: MEASURED_PEAKS.json")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--oracle-rk-steps", type=int, default=10)
+    ap.add_argument("--oracle-rk-steps", type=int, default=None,
+                    help="RK steps per oracle sample of the reference arm (default: the workload's own)")
     ap.add_argument("--rk-steps", type=int, default=None,
                     help="override the workload's RK step count (profiling runs only; not a bench number)")
     ap.add_argument("--no-extras", action="store_true")
@@ -615,7 +769,8 @@ def main():
     ap.add_argument("--profile-every", type=int, default=64, help="time one launch in this many per kernel kind")
     ap.add_argument("--no-graph", action="store_true", help="launch on the stream instead of replaying a CUDA graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--oracle-sample", nargs=2, metavar=("WORKLOAD", "RK_STEPS"), help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-sample", nargs=4, metavar=("WORKLOAD", "RK_STEPS", "REPS", "PROCS"),
+                    help=argparse.SUPPRESS)
     ap.add_argument("--order-sweep", action="store_true",
                     help="standalone 3D F and J^T throughput over N in {3,5,7,9,11,15} at ~34M unknowns")
     ap.add_argument("--ops-once", nargs=4, metavar=("DIM", "E", "N", "PRECISION"),
@@ -623,7 +778,8 @@ def main():
     args = ap.parse_args()
 
     if args.oracle_sample:
-        print(json.dumps(oracle_sample(args.oracle_sample[0], int(args.oracle_sample[1]))))
+        wl, k, reps, procs = args.oracle_sample
+        print(json.dumps(oracle_sample(wl, int(k), int(reps), int(procs))))
         return
     if args.order_sweep:
         order_sweep()
