@@ -526,6 +526,8 @@ def gpu_arm(args, world, rank, local):
     else:
         s = Sem(w["dim"], w["E"], w["N"], w["nu"], precision=args.precision, ckpt=w["ckpt"], ckpt_slots=w["slots"],
                 device=dev)
+        if args.contraction != "cuda_core":
+            s.set_contraction(args.contraction)
         x = s.coords()
         u0_h = torch.from_numpy(inputs.workload_field(w["dim"], x, inputs.SEED_U0)).pin_memory()
         uo_h = torch.from_numpy(inputs.workload_field(w["dim"], x, inputs.SEED_UOBS)).pin_memory()
@@ -604,7 +606,8 @@ def gpu_arm(args, world, rank, local):
            "config": {"workload": w["desc"], "dim": w["dim"], "E": w["E"], "N": w["N"], "unknowns": s.ndof,
                       "instances": units,
                       "scheme": scheme, "dt": dt, "rk_steps": nsteps, "trajectory": w["ckpt"],
-                      "precision": args.precision, "parallelism": "replicas" if world > 1 else "single GPU",
+                      "precision": args.precision, "contraction": args.contraction,
+                      "parallelism": "replicas" if world > 1 else "single GPU",
                       "l2": "inputs larger than L2: every step writes and re-reads the stored trajectory "
                             "(%.1f GB: %s)" % (traj_gb, w["ckpt"])},
            "roofline": roof, "gpu_launches": launches, "clocks": clk.summary(), "J": J,
@@ -732,6 +735,49 @@ def order_sweep(precisions=("fp64", "fp64_df", "fp32_bulk"), target=34e6, reps=1
     return rows
 
 
+def contraction_ab(reps=20):
+    """Standalone F(u) at 16^3 hexes, N = 15 with each contraction engine and precision: apply time,
+    sampled element-pass and assembly times, and the result against the CUDA-core engine."""
+    import torch
+    from paper_1806_01422_gb300 import Sem, inputs
+    rows = []
+    for prec in ("fp64", "fp32_bulk"):
+        s = Sem(3, 16, 15, 2e-4, precision=prec)
+        u = torch.from_numpy(inputs.field_3d(s.coords(), inputs.SEED_U0)).cuda()
+        out = s.empty()
+        ref = None
+        for mode in ("cuda_core", "tensor"):
+            s.set_contraction(mode)
+            for _ in range(3):
+                s.rhs(u, out)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                s.rhs(u, out)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            s.profile(1)
+            for _ in range(reps):
+                s.rhs(u, out)
+            torch.cuda.synchronize()
+            s.profile(0)
+            prof = s.profile_read(reset=True)
+            if ref is None:
+                ref = out.clone()
+            row = {"precision": prec, "contraction": mode, "F_ms": ms, "gdofs_F": s.ndof / ms / 1e6,
+                   "elem_us": prof["rhs"][0] / max(prof["rhs"][1], 1) * 1e3,
+                   "assemble_us": prof["assemble"][0] / max(prof["assemble"][1], 1) * 1e3,
+                   "rel_diff_vs_cuda_core": float((out - ref).abs().max() / ref.abs().max())}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+        s.close()
+        del u, out
+        torch.cuda.empty_cache()
+    return rows
+
+
 def ops_once(dim, E, N, precision):
     """One F and one J^T apply (for ncu captures of the element and assembly kernels)."""
     import torch
@@ -757,6 +803,10 @@ def main():
     ap.add_argument("--extra-reps", type=int, default=3,
                     help="timed repetitions of the other precision forms and of the end-to-end leg (at most --steps)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_bulk", "fp64_df"])
+    ap.add_argument("--contraction", default="cuda_core", choices=["cuda_core", "tensor"],
+                    help="element-kernel contraction engine (tensor: 3D, N=15 only)")
+    ap.add_argument("--contraction-ab", action="store_true",
+                    help="A/B of the contraction engines: standalone F at 16^3 hexes, N=15, FP64 and FP32-bulk")
     ap.add_argument("--hbm-peak", type=float, default=None, help="GB/s; default: MEASURED_PEAKS.json")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--oracle-rk-steps", type=int, default=None,
@@ -783,6 +833,9 @@ def main():
         return
     if args.order_sweep:
         order_sweep()
+        return
+    if args.contraction_ab:
+        contraction_ab()
         return
     if args.ops_once:
         ops_once(int(args.ops_once[0]), int(args.ops_once[1]), int(args.ops_once[2]), args.ops_once[3])

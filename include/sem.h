@@ -194,6 +194,21 @@ int sem_sweep_stats(sem_t h, long long* out3);
  * forward sweep and any recorded gradient graph. */
 int sem_set_advection(sem_t h, const double* a, void* stream);
 
+/* Contraction engine of the element kernels (no counterpart in the paper, whose
+ * element products are BLAS calls, Sec. 3.3 and 6.3).
+ * SEM_CONTRACT_CUDA_CORE (default): the 1D contractions are even-odd split FMA
+ * chains on the CUDA cores.  SEM_CONTRACT_TENSOR: for 3D handles of order N = 15
+ * (16 points per direction), the F(u) element pass applies each 16 x 16 matrix to
+ * the 256 lines of a direction as one matrix product on the tensor cores: tcgen05
+ * MMAs with split-TF32 operands and FP32 accumulation in the FP32-bulk form
+ * (three TF32 products per contraction, near FP32 accuracy), DMMA (mma.sync
+ * m8n8k4, FP64) in the FP64 form.  J and J^T keep the CUDA-core kernels.  Returns
+ * SEM_ERR_ARG for other grids, for FP64-DF and for batch handles.  Discards a
+ * recorded gradient graph. */
+#define SEM_CONTRACT_CUDA_CORE 0
+#define SEM_CONTRACT_TENSOR    1
+int sem_set_contraction(sem_t h, int mode);
+
 /* Programmatic dependent launch (process-wide; on by default; no counterpart in
  * the paper).  Element and assembly kernels are launched with the programmatic
  * stream-serialization attribute: the next kernel's blocks may be scheduled

@@ -19,6 +19,7 @@ SEM_ERR_CUDA = -6
 
 SEM_RK4, SEM_SSPRK3, SEM_EULER, SEM_CN, SEM_BS3 = 0, 1, 2, 3, 4
 SEM_PREC_FP64, SEM_PREC_FP32_BULK, SEM_PREC_FP64_DF = 0, 1, 2
+SEM_CONTRACT_CUDA_CORE, SEM_CONTRACT_TENSOR = 0, 1
 SEM_CKPT_AUTO, SEM_CKPT_STAGES, SEM_CKPT_STATES, SEM_CKPT_BINOMIAL, SEM_CKPT_TWO_LEVEL = 0, 1, 2, 3, 4
 
 
@@ -60,6 +61,7 @@ _SIGS = {
     "sem_set_adaptive": (_I, [_H, _D, _D]),
     "sem_launch_count": (_I, [_H, ctypes.POINTER(ctypes.c_longlong)]),
     "sem_set_dependent_launch": (_I, [_I]),
+    "sem_set_contraction": (_I, [_H, _I]),
     "sem_adaptive_steps": (_I, [_H, ctypes.POINTER(_I), ctypes.POINTER(_I), _P, _I]),
     "sem_trajectory_info": (_I, [_H, ctypes.POINTER(ctypes.c_longlong)]),
     "sem_solver_stats": (_I, [_H, ctypes.POINTER(ctypes.c_longlong)]),

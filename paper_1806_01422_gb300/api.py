@@ -156,6 +156,12 @@ class Sem:
                                            _stream(self.device)))
         return J.value, (grad.cpu() if host else grad)
 
+    def set_contraction(self, mode="cuda_core"):
+        """Contraction engine of the element kernels: "cuda_core" (even-odd FMA chains, default) or
+        "tensor" (3D, N = 15: tcgen05 split-TF32 in the FP32-bulk form, DMMA in FP64; F only)."""
+        m = {"cuda_core": L.SEM_CONTRACT_CUDA_CORE, "tensor": L.SEM_CONTRACT_TENSOR}[mode]
+        L.check(L.lib().sem_set_contraction(self._h, m))
+
     def use_graph(self, enable=True):
         """Record the gradient evaluation as a CUDA graph once and replay it (sem_set_graph)."""
         L.check(L.lib().sem_set_graph(self._h, 1 if enable else 0))

@@ -131,6 +131,7 @@ struct sem_ctx {
     BatchHost* batch = nullptr;
     int dim = 0, E = 0, N = 0, np = 0, G = 0;
     int precision = SEM_PREC_FP64, ckpt_mode = SEM_CKPT_AUTO, ckpt_slots = 0;
+    int contraction = SEM_CONTRACT_CUDA_CORE;   // sem_set_contraction
     size_t ckpt_budget = 0;
     double nu = 0, L = 0, h = 0;
     std::vector<double> xi, w, Dh, mats, mw;
@@ -408,7 +409,9 @@ int apply(sem_t h, int op, const double* u, const double* w, const Epi& ep, cuda
     SEM_TRY(prof_begin(h, op, s, slot));
     cudaError_t e;
     const double* mt = h->mats.data();
-    if (h->precision == SEM_PREC_FP64_DF) {   // double-float element arithmetic, FP64 everywhere else
+    if (h->contraction == SEM_CONTRACT_TENSOR && tc_supported(h->dim, h->np, op, f32)) {
+        e = launch_elem_tc(f32, op, mt, a, h->flag ? h->flag + 1 : nullptr, s);
+    } else if (h->precision == SEM_PREC_FP64_DF) {   // double-float element arithmetic, FP64 everywhere else
         if (h->dim == 1) e = launch_elem<dfloat, 1>(h->np, op, mt, a, s);
         else if (h->dim == 2) e = launch_elem<dfloat, 2>(h->np, op, mt, a, s);
         else e = launch_elem<dfloat, 3>(h->np, op, mt, a, s);
@@ -1877,6 +1880,21 @@ int sem_set_advection(sem_t h, const double* a, void* stream) {
     } else {
         SEM_CK(cudaMemcpyAsync(h->frozen, a, vec_bytes(h), cudaMemcpyDeviceToDevice, s));
     }
+    return SEM_OK;
+}
+
+int sem_set_contraction(sem_t h, int mode) {
+    if (!h) return fail(SEM_ERR_ARG, "null handle");
+    if (mode != SEM_CONTRACT_CUDA_CORE && mode != SEM_CONTRACT_TENSOR)
+        return fail(SEM_ERR_ARG, "unknown contraction mode %d", mode);
+    if (mode == SEM_CONTRACT_TENSOR &&
+        (h->batch || h->dim != 3 || h->np != 16 || h->precision == SEM_PREC_FP64_DF))
+        return fail(SEM_ERR_ARG, "tensor-core contractions need a 3D handle of order 15 in the FP64 or FP32-bulk form");
+    if (h->graph_exec) {
+        cudaGraphExecDestroy(h->graph_exec);
+        h->graph_exec = nullptr;
+    }
+    h->contraction = mode;
     return SEM_OK;
 }
 

@@ -15,6 +15,12 @@ namespace semk {
 template <typename T, int D>
 cudaError_t launch_elem(int np, int op, const double* mats, const ElemArgs& a, cudaStream_t s);
 
+// Tensor-core element kernels (d = 3, n = 16): tcgen05 with split TF32 operands for the
+// FP32-bulk form (fp32), DMMA for FP64.  F only; err (may be null) is set to 1 if the
+// kernel gave up waiting for its MMAs (its outputs are then NaN).
+bool tc_supported(int dim, int np, int op, bool fp32);
+cudaError_t launch_elem_tc(bool fp32, int op, const double* mats, const ElemArgs& a, unsigned* err, cudaStream_t s);
+
 // Largest supported point count per (D, T): limited by the shared-memory tiles.
 int max_np(int D, bool fp32);
 void set_pdl(bool on);   // programmatic dependent launch of element and assembly kernels
