@@ -93,9 +93,12 @@ void derivative(const std::vector<double>& x, std::vector<double>& D) {
 // Element-kernel matrices (row-major n x n, in this order):
 //   Dg  = (2/h) Dhat                                  (centro-antisymmetric)
 //   Sv  = -nu (2/h)^2 W^-1 Dhat^T W Dhat              (centro-symmetric)
-//   Svt = -nu (2/h)^2 Dhat^T W Dhat W^-1 = Sv^T       (centro-symmetric)
+//   Gv  = nu (2/h) W Dhat W^-1                        (centro-antisymmetric)
+//         so that Dd Gv = -nu (2/h)^2 Dhat^T W Dhat W^-1 = Sv^T: the viscous term of
+//         J^T and its advective flux share one divergence, Dd (Gv z + u o z)
 //   Dd  = -(2/h) Dhat^T                               (centro-antisymmetric)
-// The symmetric pair is symmetrised exactly: A[i][j] = A[n-1-i][n-1-j].
+// Sv is symmetrised exactly, A[i][j] = A[n-1-i][n-1-j], and Gv antisymmetrised,
+// A[i][j] = -A[n-1-i][n-1-j].
 void kernel_matrices(const std::vector<double>& w, const std::vector<double>& Dh, double h, double nu,
                      std::vector<double>& mats) {
     const int n = (int)w.size();
@@ -103,8 +106,8 @@ void kernel_matrices(const std::vector<double>& w, const std::vector<double>& Dh
     mats.assign((size_t)4 * n * n, 0.0);
     double* Dg = mats.data();
     double* Sv = Dg + n * n;
-    double* Svt = Sv + n * n;
-    double* Dd = Svt + n * n;
+    double* Gv = Sv + n * n;
+    double* Dd = Gv + n * n;
     std::vector<double> K((size_t)n * n, 0.0);  // Dhat^T W Dhat
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) {
@@ -116,14 +119,15 @@ void kernel_matrices(const std::vector<double>& w, const std::vector<double>& Dh
         for (int j = 0; j < n; ++j) {
             Dg[i * n + j] = s * Dh[(size_t)i * n + j];
             Sv[i * n + j] = -nu * s * s * K[(size_t)i * n + j] / w[i];
-            Svt[i * n + j] = -nu * s * s * K[(size_t)i * n + j] / w[j];
+            Gv[i * n + j] = nu * s * w[i] * Dh[(size_t)i * n + j] / w[j];
             Dd[i * n + j] = -s * Dh[(size_t)j * n + i];
         }
-    for (double* A : {Sv, Svt}) {
+    for (double* A : {Sv, Gv}) {
+        const double sign = A == Sv ? 1.0 : -1.0;
         std::vector<double> S(A, A + n * n);
         for (int i = 0; i < n; ++i)
             for (int j = 0; j < n; ++j)
-                A[i * n + j] = 0.5 * (S[(size_t)i * n + j] + S[(size_t)(n - 1 - i) * n + (n - 1 - j)]);
+                A[i * n + j] = 0.5 * (S[(size_t)i * n + j] + sign * S[(size_t)(n - 1 - i) * n + (n - 1 - j)]);
     }
 }
 

@@ -32,7 +32,7 @@ cudaError_t launch_elem_tc(bool fp32, int op, const double* mats, const ElemArgs
     FullMats16 FM;
     std::memcpy(FM.Dg, mats + 0 * 256, sizeof(FM.Dg));
     std::memcpy(FM.Sv, mats + 1 * 256, sizeof(FM.Sv));
-    std::memcpy(FM.Svt, mats + 2 * 256, sizeof(FM.Svt));
+    std::memcpy(FM.Gv, mats + 2 * 256, sizeof(FM.Gv));
     std::memcpy(FM.Dd, mats + 3 * 256, sizeof(FM.Dd));
     if (a.nelem <= 0) return cudaSuccess;
     static thread_local unsigned long long done_f = 0, done_d = 0;

@@ -8,8 +8,8 @@
 // Local results (see op_kernels.cuh for the matrices):
 //   F :  f_c   = sum_j [ Sv_j U_c - U_j Dg_j U_c ]
 //   J :  f_c   = sum_j [ Sv_j W_c - (W_j Dg_j U_c + U_j Dg_j W_c) ]
-//   JT:  f_l   = sum_j [ Svt_j Z_l + Dd_j (U_j Z_l) ] - sum_c Z_c Dg_l U_c,   Z = v / k
-// with Dg_j, Sv_j, Svt_j, Dd_j the 1D matrices applied along direction x_j.  Each
+//   JT:  f_l   = sum_j Dd_j (Gv_j Z_l + U_j Z_l) - sum_c Z_c Dg_l U_c,   Z = v / k
+// with Dg_j, Sv_j, Gv_j, Dd_j the 1D matrices applied along direction x_j.  Each
 // bracket is one pass along direction j; in 3D the x and y passes write two
 // partial-result tiles and the z pass adds them and writes the result.
 #pragma once
@@ -59,6 +59,16 @@ __device__ __forceinline__ T inv_mult(int nb) {
     return nb == 0 ? (T)1 : (nb == 1 ? (T)0.5 : (nb == 2 ? (T)0.25 : (T)0.125));
 }
 
+// x * 2^-nb (nb = 0..3) without an FP64 instruction: the exponent field is lowered with
+// integer arithmetic, which is exact.  Zeros, subnormal results, infinities and NaNs (rare)
+// take the multiply, which gives the same value.
+__device__ __forceinline__ double scale_pow2_down(double x, int nb) {
+    const long long b = __double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    if (ex > nb && ex != 0x7ff) return __longlong_as_double(b - ((long long)nb << 52));
+    return x * inv_mult<double>(nb);
+}
+
 // Value stored in a tile for global node i: the input (FP64), U - U_ref (FP32), or
 // v / k when scale_mult (nb = boundary count of the node, k = 2^nb).
 template <typename T>
@@ -77,7 +87,7 @@ __device__ __forceinline__ T tile_value(const ElemArgs& a, const void* g, size_t
         return dfloat(h, l);
     } else if constexpr (sizeof(T) == 8) {
         const double x = __ldg((const double*)g + i);
-        return scale_mult ? x * inv_mult<double>(nb) : x;
+        return scale_mult ? scale_pow2_down(x, nb) : x;
     } else {
         float hi, lo;
         read_pair(a, g, i, hi, lo);
@@ -99,7 +109,7 @@ __device__ __forceinline__ T tile_of_double(double x, bool scale_mult, int nb) {
         }
         return dfloat(h, l);
     } else {
-        return scale_mult ? x * inv_mult<double>(nb) : x;
+        return scale_mult ? scale_pow2_down(x, nb) : x;
     }
 }
 
@@ -152,6 +162,17 @@ __device__ __forceinline__ T load3(T* tile, const void* g, int c, int ex, int ey
         for (int k = 0; k < NP; ++k)
             tile[(k * NP + j) * Tl::P + i] = tile_of_double<T>(xv[k], scale_mult, nbij + (int)(k == 0 || k == N));
         return (T)ref_hi;
+    }
+}
+
+// Load the three components of u (and of the second input) of a d = 3 element.
+template <typename T, int NP>
+__device__ __forceinline__ void load3_fields(T* const* sU, T* const* sV, const ElemArgs& a, int ex, int ey, int ez,
+                                             int t, bool valid, T* rU, T* rV, bool v_is_z) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        rU[c] = load3<T, NP>(sU[c], a.u, c, ex, ey, ez, t, valid, a, false);
+        if (sV) rV[c] = load3<T, NP>(sV[c], a.w, c, ex, ey, ez, t, valid, a, v_is_z);
     }
 }
 
@@ -243,18 +264,16 @@ __device__ __forceinline__ void jac_pass(const OpMats<T, NP>& M, const T* sUc, c
     }
 }
 
-// One J^T pass: r = Svt Z_l + Dd (U_d Z_l), plus -sum_c Z_c Dg U_c when d == l.
+// One J^T pass: r = Dd (Gv Z_l + U_d Z_l), plus -sum_c Z_c Dg U_c when d == l.
 template <typename T, int NP, int STRIDE, int D>
 __device__ __forceinline__ void jact_pass(const OpMats<T, NP>& M, T* const* sU, T* const* sZ, const T* rU,
                                           int l, int d, int base, T (&r)[NP]) {
-    T z[NP], q[NP], dv[NP];
+    T z[NP], q[NP];
     ld_line<T, NP, STRIDE>(sZ[l], base, z);
-    eo_apply<true, T, NP>(M.Svt, z, r);
+    eo_apply<false, T, NP>(M.Gv, z, q);
 #pragma unroll
-    for (int m = 0; m < NP; ++m) q[m] = with_ref(rU[d], sU[d][base + m * STRIDE]) * z[m];
-    eo_apply<false, T, NP>(M.Dd, q, dv);
-#pragma unroll
-    for (int m = 0; m < NP; ++m) r[m] += dv[m];
+    for (int m = 0; m < NP; ++m) q[m] = fma(with_ref(rU[d], sU[d][base + m * STRIDE]), z[m], q[m]);
+    eo_apply<false, T, NP>(M.Dd, q, r);
     if (l == d) {
 #pragma unroll
         for (int c = 0; c < D; ++c) {
@@ -371,8 +390,7 @@ __global__ void rhs3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
     T* sA = sm + 4 * S3;
     const int ex = e % a.E, ey = (e / a.E) % a.E, ez = e / (a.E * a.E);
     T rU[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) rU[c] = load3<T, NP>(sU[c], a.u, c, ex, ey, ez, t, valid, a, false);
+    load3_fields<T, NP>(sU, nullptr, a, ex, ey, ez, t, valid, rU, nullptr, false);
     __syncthreads();
     pdl_trigger();
     if constexpr (shared_pass3<T, NP>()) {
@@ -414,11 +432,7 @@ __global__ void jac3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
     T* sA = sm + 7 * S3;
     const int ex = e % a.E, ey = (e / a.E) % a.E, ez = e / (a.E * a.E);
     T rU[3], rW[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        rU[c] = load3<T, NP>(sU[c], a.u, c, ex, ey, ez, t, valid, a, false);
-        rW[c] = load3<T, NP>(sW[c], a.w, c, ex, ey, ez, t, valid, a, false);
-    }
+    load3_fields<T, NP>(sU, sW, a, ex, ey, ez, t, valid, rU, rW, false);
     __syncthreads();
     pdl_trigger();
     if constexpr (shared_pass3<T, NP>()) {
@@ -459,12 +473,8 @@ __global__ void jact3_kernel(const __grid_constant__ OpMats<T, NP> M, const Elem
     T* sF = sm + 6 * S3;
     T* sA = sm + 7 * S3;
     const int ex = e % a.E, ey = (e / a.E) % a.E, ez = e / (a.E * a.E);
-    T rU[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        rU[c] = load3<T, NP>(sU[c], a.u, c, ex, ey, ez, t, valid, a, false);
-        load3<T, NP>(sZ[c], a.w, c, ex, ey, ez, t, valid, a, true);
-    }
+    T rU[3], rZ[3];
+    load3_fields<T, NP>(sU, sZ, a, ex, ey, ez, t, valid, rU, rZ, true);
     __syncthreads();
     pdl_trigger();
     if constexpr (shared_pass3<T, NP>()) {
@@ -691,15 +701,13 @@ __device__ __forceinline__ void jac2c_body(const OpMats<T, NP>& M, const ElemArg
 template <typename T, int NP, int D>
 __device__ __forceinline__ void jact_pass_rt(const OpMats<T, NP>& M, T* const* sU, T* const* sZ, const T* rU, int l,
                                              int d, int base, int stride, T (&r)[NP]) {
-    T z[NP], q[NP], dv[NP];
+    T z[NP], q[NP];
 #pragma unroll
     for (int m = 0; m < NP; ++m) z[m] = sZ[l][base + m * stride];
-    eo_apply<true, T, NP>(M.Svt, z, r);
+    eo_apply<false, T, NP>(M.Gv, z, q);
 #pragma unroll
-    for (int m = 0; m < NP; ++m) q[m] = with_ref(rU[d], sU[d][base + m * stride]) * z[m];
-    eo_apply<false, T, NP>(M.Dd, q, dv);
-#pragma unroll
-    for (int m = 0; m < NP; ++m) r[m] += dv[m];
+    for (int m = 0; m < NP; ++m) q[m] = fma(with_ref(rU[d], sU[d][base + m * stride]), z[m], q[m]);
+    eo_apply<false, T, NP>(M.Dd, q, r);
     if (l == d) {
 #pragma unroll 1
         for (int c = 0; c < D; ++c) {
@@ -799,15 +807,15 @@ __global__ void op1_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemAr
 #pragma unroll
         for (int m = 0; m < NP; ++m) f[m] -= fma(with_ref(rw, w[m]), gu[m], with_ref(ru, u[m]) * gw[m]);
     } else {
-        T z[NP], q[NP], dv[NP], gu[NP];
+        T z[NP], q[NP], gu[NP];
         load1<T, NP>(z, a.w, e, a, true);
-        eo_apply<true, T, NP>(M.Svt, z, f);
+        eo_apply<false, T, NP>(M.Gv, z, q);
 #pragma unroll
-        for (int m = 0; m < NP; ++m) q[m] = with_ref(ru, u[m]) * z[m];
-        eo_apply<false, T, NP>(M.Dd, q, dv);
+        for (int m = 0; m < NP; ++m) q[m] = fma(with_ref(ru, u[m]), z[m], q[m]);
+        eo_apply<false, T, NP>(M.Dd, q, f);
         eo_apply<false, T, NP>(M.Dg, u, gu);
 #pragma unroll
-        for (int m = 0; m < NP; ++m) f[m] = fma(-z[m], gu[m], f[m] + dv[m]);
+        for (int m = 0; m < NP; ++m) f[m] = fma(-z[m], gu[m], f[m]);
     }
     auto* o = reinterpret_cast<typename OutT<T>::type*>(a.lvec) + (size_t)e * NP;
 #pragma unroll

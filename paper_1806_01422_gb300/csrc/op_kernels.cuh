@@ -15,12 +15,14 @@
 // the 1D second-derivative matrix Sv = -nu (2/h)^2 W^-1 Dhat^T W Dhat, applied
 // along j: every mass factor folds into 1D matrices.  For the transpose, with
 // zhat = v / k (so B z = zhat for z = M^-1 v):
-//   (L^T z)_l = sum_j [ Svt_j zhat_l + Dd_j (U_j zhat_l) ] - sum_c zhat_c Dg_l U_c,
-// Svt = -nu (2/h)^2 Dhat^T W Dhat W^-1, Dd = -(2/h) Dhat^T, Dg = (2/h) Dhat.
+//   (L^T z)_l = sum_j Dd_j (Gv_j zhat_l + U_j zhat_l) - sum_c zhat_c Dg_l U_c,
+// Gv = nu (2/h) W Dhat W^-1, Dd = -(2/h) Dhat^T, Dg = (2/h) Dhat: the viscous flux
+// and the advective flux of J^T share one divergence contraction (Dd Gv is the
+// viscous matrix -nu (2/h)^2 Dhat^T W Dhat W^-1).
 //
-// Dg and Dd are centro-antisymmetric (A[n-1-i][n-1-j] = -A[i][j], because the
-// GLL nodes are symmetric) and Sv, Svt are centro-symmetric (products of two
-// such matrices), so a contraction of a line of n values costs n^2/2
+// Dg, Dd and Gv are centro-antisymmetric (A[n-1-i][n-1-j] = -A[i][j], because the
+// GLL nodes are symmetric) and Sv is centro-symmetric (a product of two such
+// matrices), so a contraction of a line of n values costs n^2/2
 // multiply-adds plus n adds, with the n pre-adds shared by every matrix
 // applied to the same line (even-odd split).
 //
@@ -65,7 +67,7 @@ template <typename T, int NP>
 struct OpMats {
     EOMat<T, NP> Dg;   // (2/h) Dhat                                antisymmetric: gradient
     EOMat<T, NP> Sv;   // -nu (2/h)^2 W^-1 Dhat^T W Dhat             symmetric: viscous term of F and J
-    EOMat<T, NP> Svt;  // -nu (2/h)^2 Dhat^T W Dhat W^-1             symmetric: viscous term of J^T
+    EOMat<T, NP> Gv;   // nu (2/h) W Dhat W^-1                       antisymmetric: viscous flux of J^T
     EOMat<T, NP> Dd;   // -(2/h) Dhat^T                              antisymmetric: divergence (J^T)
 };
 

@@ -48,7 +48,7 @@ cudaError_t launch_elem_np(int op, const double* mats, const ElemArgs& a, cudaSt
     OpMats<T, NP> M;
     split_eo<T, NP>(M.Dg, mats + 0 * NP * NP);
     split_eo<T, NP>(M.Sv, mats + 1 * NP * NP);
-    split_eo<T, NP>(M.Svt, mats + 2 * NP * NP);
+    split_eo<T, NP>(M.Gv, mats + 2 * NP * NP);
     split_eo<T, NP>(M.Dd, mats + 3 * NP * NP);
     if (a.nelem <= 0) return cudaSuccess;
     if constexpr (D == 1) {

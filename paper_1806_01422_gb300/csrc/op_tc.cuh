@@ -34,7 +34,7 @@ namespace semk {
 struct FullMats16 {
     double Dg[16][16];
     double Sv[16][16];
-    double Svt[16][16];
+    double Gv[16][16];
     double Dd[16][16];
 };
 

@@ -10,7 +10,7 @@ struct sem_ctx;
 namespace semk {
 
 // Element kernel launch for dimension D, compute type T, runtime point count
-// np = N+1.  `mats` holds the four full np x np matrices Dg, Dv, Vz, Dd
+// np = N+1.  `mats` holds the four full np x np matrices Dg, Sv, Gv, Dd
 // (row-major, in that order); the launcher splits them into even/odd halves.
 template <typename T, int D>
 cudaError_t launch_elem(int np, int op, const double* mats, const ElemArgs& a, cudaStream_t s);

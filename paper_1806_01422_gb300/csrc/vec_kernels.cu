@@ -237,6 +237,184 @@ __global__ void __launch_bounds__(128) assemble_f32_kernel(const float* __restri
     }
 }
 
+// Row-wise FP32 assembly for d = 3 (n = 8 and n = 16).  The node kernel above
+// spends most of its issue slots on per-node index arithmetic; here one warp owns
+// a chunk of one grid row along x (component c, rows gy and gz, up to 32
+// elements along x) and the index work is done once per row.
+//  * Gather: lane l takes element ex = 32 chunk + l and loads its element-local
+//    row (n floats, vector loads) from each (y, z) element pair that shares the
+//    row (1, 2 or 4 of them); node N of the left neighbour's row comes from lane
+//    l - 1 by a shuffle (lane 0 loads it).  Its N nodes are summed in the order
+//    of gather_node, so the results are the node kernel's bits.
+//  * Epilogue: the sums go through shared memory and the warp walks the row's
+//    nodes in order, lane l taking nodes l, l + 32, .., so that the sources and
+//    outputs are read and written with coalesced accesses.
+constexpr int ROW_WARPS = 8;
+
+template <int NP>
+__device__ __forceinline__ void load_row(const float* __restrict__ p, float (&v)[NP]) {
+    static_assert(NP % 4 == 0, "vector loads of whole rows");
+#pragma unroll
+    for (int q = 0; q < NP / 4; ++q) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(p) + q);
+        v[4 * q] = t.x;
+        v[4 * q + 1] = t.y;
+        v[4 * q + 2] = t.z;
+        v[4 * q + 3] = t.w;
+    }
+}
+
+template <int NP, int NOUT, int NSRC, bool F2>
+__global__ void __launch_bounds__(32 * ROW_WARPS) assemble_rows_f32_kernel(const float* __restrict__ lvec,
+                                                                           const AsmArgs a, const EpiF2 ep,
+                                                                           int nchunk) {
+    constexpr int N = NP - 1;
+    constexpr unsigned NPD = NP * NP * NP;
+    __shared__ float srow[ROW_WARPS][32 * N];
+    pdl_wait();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned task = blockIdx.x * ROW_WARPS + warp;     // (c, gz, gy, chunk), chunk fastest
+    if (task >= 3u * a.G * a.G * nchunk) return;            // whole warps only
+    const int chunk = task % nchunk;
+    unsigned rest = task / nchunk;
+    const int gy = rest % a.G;
+    rest /= a.G;
+    const int gz = rest % a.G;
+    const int c = rest / a.G;
+    const AxisSplit sy = axis_split(gy, a), sz = axis_split(gz, a);
+    const int ex = chunk * 32 + lane;
+    const bool act = ex < a.E;
+    const int exs = act ? ex : a.E - 1;                       // idle lanes re-read a valid row
+    auto row = [&](int exx, int ey, int j, int ez, int k) -> const float* {
+        const unsigned el = ((unsigned)ez * a.E + ey) * a.E + exx;
+        return lvec + ((size_t)el * 3 + c) * NPD + (k * NP + j) * NP;
+    };
+    const int exl = chunk * 32 == 0 ? a.E - 1 : chunk * 32 - 1;   // left neighbour of lane 0
+    float v00[NP], v10[NP], v01[NP], v11[NP];
+    float l00, l10 = 0.f, l01 = 0.f, l11 = 0.f;
+    load_row<NP>(row(exs, sy.e0, sy.i0, sz.e0, sz.i0), v00);
+    float t0 = lane == 0 ? row(exl, sy.e0, sy.i0, sz.e0, sz.i0)[N] : 0.f;
+    l00 = __shfl_up_sync(0xffffffffu, v00[N], 1);
+    if (lane == 0) l00 = t0;
+    if (sy.sh) {
+        load_row<NP>(row(exs, sy.e1, N, sz.e0, sz.i0), v10);
+        t0 = lane == 0 ? row(exl, sy.e1, N, sz.e0, sz.i0)[N] : 0.f;
+        l10 = __shfl_up_sync(0xffffffffu, v10[N], 1);
+        if (lane == 0) l10 = t0;
+    }
+    if (sz.sh) {
+        load_row<NP>(row(exs, sy.e0, sy.i0, sz.e1, N), v01);
+        t0 = lane == 0 ? row(exl, sy.e0, sy.i0, sz.e1, N)[N] : 0.f;
+        l01 = __shfl_up_sync(0xffffffffu, v01[N], 1);
+        if (lane == 0) l01 = t0;
+        if (sy.sh) {
+            load_row<NP>(row(exs, sy.e1, N, sz.e1, N), v11);
+            t0 = lane == 0 ? row(exl, sy.e1, N, sz.e1, N)[N] : 0.f;
+            l11 = __shfl_up_sync(0xffffffffu, v11[N], 1);
+            if (lane == 0) l11 = t0;
+        }
+    }
+    if (act) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            // gather_node's order: x pairs first, then the y pair, then the z pairs
+            float sum = i == 0 ? v00[0] + l00 : v00[i];
+            if (sy.sh) sum += i == 0 ? v10[0] + l10 : v10[i];
+            if (sz.sh) {
+                float t = i == 0 ? v01[0] + l01 : v01[i];
+                if (sy.sh) t += i == 0 ? v11[0] + l11 : v11[i];
+                sum += t;
+            }
+            srow[warp][lane * N + i] = sum;
+        }
+    }
+    __syncwarp();
+    const int nodes = min(32, a.E - chunk * 32) * N;
+    const unsigned base = c * a.GD + ((unsigned)gz * a.G + gy) * a.G + chunk * 32 * N;
+    const int nsh_yz = (int)sy.sh + (int)sz.sh;
+    bool bad = false;
+    if constexpr (!F2) {
+        for (int q = lane; q < nodes; q += 32) {
+            const float sum = srow[warp][q];
+            const int nsh = nsh_yz + (int)(q % N == 0);
+            const float v = a.scale_mult ? sum * (nsh == 0 ? 1.f : (nsh == 1 ? 0.5f : (nsh == 2 ? 0.25f : 0.125f)))
+                                         : sum;
+            ep.out_f64[base + q] = widen_bits(v);
+            bad |= nonfinite_f(v);
+        }
+    } else {
+        // batches of B nodes per lane: every source of the batch is read before any output is
+        // written (an output may be a source, in place), so the loads of a batch overlap
+        constexpr int B = NSRC >= 3 ? 2 : 4;
+        for (int q0 = lane; q0 < nodes; q0 += 32 * B) {
+            df sv[B][NSRC > 0 ? NSRC : 1];
+            float sum[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int q = q0 + 32 * b;
+                const bool live = q < nodes;
+                sum[b] = live ? srow[warp][q] : 0.f;
+#pragma unroll
+                for (int m = 0; m < NSRC; ++m)
+                    sv[b][m] = live ? df{ep.src[m][base + q], ep.src[m][ep.plane + base + q]} : df{0.f, 0.f};
+            }
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int q = q0 + 32 * b;
+                if (q >= nodes) break;
+                const int nsh = nsh_yz + (int)(q % N == 0);
+                df ov[NOUT];
+#pragma unroll
+                for (int o = 0; o < NOUT; ++o) {
+                    df v = df_mul_f(pick4(ep.alpha_k[o], nsh), sum[b]);
+#pragma unroll
+                    for (int m = 0; m < NSRC; ++m) v = df_add(v, df_mul(ep.beta[o][m], sv[b][m]));
+                    ov[o] = v;
+                    bad |= nonfinite_f(v.hi);
+                }
+#pragma unroll
+                for (int o = 0; o < NOUT; ++o) {
+                    ep.out[o][base + q] = ov[o].hi;
+                    ep.out[o][ep.plane + base + q] = ov[o].lo;
+                }
+            }
+        }
+    }
+    if (bad && ep.nonfinite) atomicOr(ep.nonfinite, 1u);
+}
+
+template <int NP, int NOUT, int NSRC, bool F2>
+cudaError_t launch_rows_f32(const float* lvec, const AsmArgs& a, const EpiF2& e2, cudaStream_t s) {
+    const int nchunk = (a.E + 31) / 32;
+    const unsigned tasks = 3u * a.G * a.G * nchunk;
+    const unsigned blocks = (tasks + ROW_WARPS - 1) / ROW_WARPS;
+    return launch_pdl(assemble_rows_f32_kernel<NP, NOUT, NSRC, F2>, dim3(blocks), dim3(32 * ROW_WARPS), 0, s, lvec,
+                      a, e2, nchunk);
+}
+
+// The row kernel serves these point counts (n a multiple of 4 for the vector loads).
+__host__ __device__ constexpr bool rows_f32_np(int np) { return np == 8 || np == 16; }
+
+template <int NP>
+cudaError_t dispatch_rows_f32(const float* lvec, const AsmArgs& a, const EpiF2& e2, int nout, int nsrc, bool f2,
+                              cudaStream_t s) {
+    if (!f2) return launch_rows_f32<NP, 1, 0, false>(lvec, a, e2, s);
+#define SEMK_ROWS_NS(NO)                                                        \
+    switch (nsrc) {                                                             \
+        case 0: return launch_rows_f32<NP, NO, 0, true>(lvec, a, e2, s);        \
+        case 1: return launch_rows_f32<NP, NO, 1, true>(lvec, a, e2, s);        \
+        case 2: return launch_rows_f32<NP, NO, 2, true>(lvec, a, e2, s);        \
+        case 3: return launch_rows_f32<NP, NO, 3, true>(lvec, a, e2, s);        \
+        default: return launch_rows_f32<NP, NO, 4, true>(lvec, a, e2, s);       \
+    }
+    switch (nout) {
+        case 1: SEMK_ROWS_NS(1)
+        case 2: SEMK_ROWS_NS(2)
+        default: SEMK_ROWS_NS(3)
+    }
+#undef SEMK_ROWS_NS
+}
+
 static std::atomic<bool> g_pdl{true};
 bool pdl_enabled() { return g_pdl.load(std::memory_order_relaxed); }
 void set_pdl(bool on) { g_pdl.store(on, std::memory_order_relaxed); }
@@ -310,6 +488,8 @@ cudaError_t launch_assemble(bool lvec_fp32, const void* lvec, const AsmArgs& a_i
             e2.nonfinite = ep.nonfinite;
             if (a.D == 1) return launch_pdl(assemble_f32_kernel<1, 1, 0, false>, grid, dim3(threads), 0, s, (const float*)lvec, a, e2);
             if (a.D == 2) return launch_pdl(assemble_f32_kernel<2, 1, 0, false>, grid, dim3(threads), 0, s, (const float*)lvec, a, e2);
+            if (a.NP == 8) return dispatch_rows_f32<8>((const float*)lvec, a, e2, 1, 0, false, s);
+            if (a.NP == 16) return dispatch_rows_f32<16>((const float*)lvec, a, e2, 1, 0, false, s);
             return launch_pdl(assemble_f32_kernel<3, 1, 0, false>, grid, dim3(threads), 0, s, (const float*)lvec, a, e2);
         }
         EpiF2 e2{};
@@ -335,6 +515,8 @@ cudaError_t launch_assemble(bool lvec_fp32, const void* lvec, const AsmArgs& a_i
         case 2: SEMK_F2_NS(D, 2) break;       \
         default: SEMK_F2_NS(D, 3) break;      \
     }
+        if (a.D == 3 && a.NP == 8) return dispatch_rows_f32<8>((const float*)lvec, a, e2, ep.nout, ep.nsrc, true, s);
+        if (a.D == 3 && a.NP == 16) return dispatch_rows_f32<16>((const float*)lvec, a, e2, ep.nout, ep.nsrc, true, s);
         if (a.D == 1) { SEMK_F2_NO(1) }
         else if (a.D == 2) { SEMK_F2_NO(2) }
         else { SEMK_F2_NO(3) }
