@@ -446,6 +446,8 @@ def roofline_of(prof, args, w, s, precision):
         peak = PEAK_FP32_TFLOPS if fp32 else (PEAK_DF_TFLOPS if dfk else PEAK_FP64_TFLOPS)
         ctype = "float" if fp32 else ("semk::dfa::dfloat" if dfk else "double")
         kernel = kname or "%s%d_kernel<%s,%d>" % (names[dom], w["dim"], ctype, w["N"] + 1)
+        if w["dim"] == 3 and ctype == "double" and w["N"] == 7 and not kname:
+            kernel = "%s3_f64_kernel<8>" % names[dom]     # the register-capped FP64 n = 8 kernels
         if dfk and w["dim"] == 2:
             kernel = "op2c_kernel<%s,%d> (%s)" % (ctype, w["N"] + 1, {"rhs": "F", "jac": "J", "jacT": "J^T"}[dom])
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -778,11 +780,13 @@ def contraction_ab(reps=20):
     return rows
 
 
-def ops_once(dim, E, N, precision):
+def ops_once(dim, E, N, precision, contraction="cuda_core"):
     """One F and one J^T apply (for ncu captures of the element and assembly kernels)."""
     import torch
     from paper_1806_01422_gb300 import Sem, inputs
     s = Sem(dim, E, N, 1e-3, precision=precision)
+    if contraction != "cuda_core":
+        s.set_contraction(contraction)
     x = s.coords()
     u = torch.from_numpy(inputs.workload_field(dim, x, inputs.SEED_U0)).cuda()
     v = torch.from_numpy(inputs.workload_field(dim, x, inputs.SEED_UOBS)).cuda()
@@ -790,7 +794,7 @@ def ops_once(dim, E, N, precision):
     s.rhs(u, out)
     s.jacT(u, v, out)
     torch.cuda.synchronize()
-    print(json.dumps({"ops_once": [dim, E, N, precision], "unknowns": s.ndof}))
+    print(json.dumps({"ops_once": [dim, E, N, precision, contraction], "unknowns": s.ndof}))
 
 
 def main():
@@ -838,7 +842,8 @@ def main():
         contraction_ab()
         return
     if args.ops_once:
-        ops_once(int(args.ops_once[0]), int(args.ops_once[1]), int(args.ops_once[2]), args.ops_once[3])
+        ops_once(int(args.ops_once[0]), int(args.ops_once[1]), int(args.ops_once[2]), args.ops_once[3],
+                 args.contraction)
         return
     if args.rk_steps:
         for w in WORKLOADS.values():

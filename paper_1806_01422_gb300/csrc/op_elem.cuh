@@ -376,7 +376,7 @@ __device__ __forceinline__ void df3_body(const OpMats<T, NP>& M, const ElemArgs&
 }
 
 template <typename T, int NP>
-__global__ void rhs3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
+__device__ __forceinline__ void rhs3_body(const OpMats<T, NP>& M, const ElemArgs& a) {
     using Tl = Tile<NP>;
     constexpr int TPE = NP * NP, P = Tl::P, S2 = Tl::S2, S3 = Tl::S3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -417,7 +417,7 @@ __global__ void rhs3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
 }
 
 template <typename T, int NP>
-__global__ void jac3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
+__device__ __forceinline__ void jac3_body(const OpMats<T, NP>& M, const ElemArgs& a) {
     using Tl = Tile<NP>;
     constexpr int TPE = NP * NP, P = Tl::P, S2 = Tl::S2, S3 = Tl::S3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -459,7 +459,7 @@ __global__ void jac3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemA
 }
 
 template <typename T, int NP>
-__global__ void jact3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
+__device__ __forceinline__ void jact3_body(const OpMats<T, NP>& M, const ElemArgs& a) {
     using Tl = Tile<NP>;
     constexpr int TPE = NP * NP, P = Tl::P, S2 = Tl::S2, S3 = Tl::S3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -498,6 +498,45 @@ __global__ void jact3_kernel(const __grid_constant__ OpMats<T, NP> M, const Elem
         }
         __syncthreads();
     }
+}
+
+template <typename T, int NP>
+__global__ void rhs3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
+    rhs3_body<T, NP>(M, a);
+}
+
+template <typename T, int NP>
+__global__ void jac3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
+    jac3_body<T, NP>(M, a);
+}
+
+template <typename T, int NP>
+__global__ void jact3_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemArgs a) {
+    jact3_body<T, NP>(M, a);
+}
+
+// FP64 with n = 8 (the order of the 3D workload): the same bodies with the registers
+// capped so that more blocks share an SM.  Uncapped, F uses 136 registers per thread and
+// one 256-thread block fits an SM (8 warps); capped at 128 (36 bytes of spill) two fit.
+// J and J^T run blocks of 128 threads (two elements): capped at 170 registers, three
+// blocks fit instead of two, with no spill.  The FP64 pipe is the bound; the extra warps
+// hide its latency.
+template <int NP>
+__global__ void __launch_bounds__(256, 2) rhs3_f64_kernel(const __grid_constant__ OpMats<double, NP> M,
+                                                          const ElemArgs a) {
+    rhs3_body<double, NP>(M, a);
+}
+
+template <int NP>
+__global__ void __launch_bounds__(128, 3) jac3_f64_kernel(const __grid_constant__ OpMats<double, NP> M,
+                                                          const ElemArgs a) {
+    jac3_body<double, NP>(M, a);
+}
+
+template <int NP>
+__global__ void __launch_bounds__(128, 3) jact3_f64_kernel(const __grid_constant__ OpMats<double, NP> M,
+                                                           const ElemArgs a) {
+    jact3_body<double, NP>(M, a);
 }
 
 // ================================================================== d = 2

@@ -77,6 +77,8 @@ cudaError_t launch_elem_np(int op, const double* mats, const ElemArgs& a, cudaSt
         if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
         const int threads = epb * TPE;
         const int blocks = (a.nelem + epb - 1) / epb;
+        if constexpr (D == 3 && std::is_same<T, double>::value && NP == 8)
+            if (threads > (op == OP_RHS ? 256 : 128)) return cudaErrorInvalidConfiguration;
         if constexpr (comp_parallel<T, D>()) {
             if (smem > 48 * 1024) {
                 static thread_local unsigned long long done_c = 0;
@@ -98,6 +100,8 @@ cudaError_t launch_elem_np(int op, const double* mats, const ElemArgs& a, cudaSt
         if constexpr (lean)
             k = op == OP_RHS ? rhs3_lean_kernel<T, NP>
                              : (op == OP_JAC ? jac3_lean_kernel<T, NP> : jact3_lean_kernel<T, NP>);
+        else if constexpr (D == 3 && std::is_same<T, double>::value && NP == 8)
+            k = op == OP_RHS ? rhs3_f64_kernel<NP> : (op == OP_JAC ? jac3_f64_kernel<NP> : jact3_f64_kernel<NP>);
         else if constexpr (D == 3)
             k = op == OP_RHS ? rhs3_kernel<T, NP> : (op == OP_JAC ? jac3_kernel<T, NP> : jact3_kernel<T, NP>);
         else
