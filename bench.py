@@ -86,6 +86,10 @@ PEAK_DF_TFLOPS = 152 * 128 * 2.07e9 / 13 * 2 / 1e12
 # DRAM traffic per launch (bytes) of the dominant kernel from one ncu capture,
 # valid only while the kernel sources hash to the recorded value.
 TRAFFIC = {
+    "rhs3_f64_kernel<8>@3d@fp64": {
+        "bytes": int(round((183180032 + 220667136) * 32 ** 3 / 28 ** 3)), "src": "a57e282a9c2aa7b5",
+        "capture": "dram__bytes_read.sum + dram__bytes_write.sum of one rhs3_f64_kernel<8> launch at 28^3 hexes, "
+                   "N=7 (ncu --set full), scaled to 32^3 hexes by the element count"},
     "jact2_kernel<double,8>@2d@fp64": {
         "bytes": 6478592 + 0, "src": "a16d1fe8a8f9f7aa",
         "capture": "dram__bytes_read.sum + dram__bytes_write.sum of one jact2 launch at 64x64 quads, N=7 "
