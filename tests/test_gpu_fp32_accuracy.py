@@ -4,22 +4,21 @@ The FP32-bulk form computes the contractions, pointwise products and element sum
 in FP32 and keeps stage accumulation, misfit and gradient sums in float pairs or
 FP64.  Its error against the FP64 form comes from the FP32 rounding of the large
 inter-element viscous fluxes of the lumped-mass weak form (Sec. 3.2), which cancel
-in the gather-scatter sum; in a sweep it adds up step by step, so it grows about
-linearly with the horizon.  Measured on GB300 (relative to the largest entry):
+in the gather-scatter sum; in a sweep it adds up step by step, so it grows with the
+horizon.  Measured on GB300 (relative to the largest entry):
 
   2D, 64^2 quads, N = 7, nu = 1e-3, SSP-RK3, dt = 2e-4 (the 2D workload):
       steps    u_N       J         gradient
-      250      9.7e-8    7.2e-9    1.4e-6
-      500      3.2e-7    1.5e-8    2.9e-6
-      1000     3.6e-6    3.3e-8    6.0e-6
-      2000     4.7e-6    3.8e-8    1.22e-5
+      250      9.7e-8    7.2e-9    8.3e-8
+      500      3.2e-7    1.5e-8    1.2e-7
+      1000     3.6e-6    3.3e-8    2.6e-7
+      2000     4.7e-6    3.8e-8    4.4e-7
   2D, 8^2 quads, N = 7, nu = 1e-2, 500 steps, against the FP64 oracle:
-               2.6e-7    5.0e-8    3.2e-7
-  3D, 32^3 hexes, N = 7, nu = 5e-4, RK4, 300 steps: J 1.2e-8, gradient 3.5e-7.
+               2.6e-7    5.0e-8    6.7e-8
+  3D, 32^3 hexes, N = 7, nu = 5e-4, RK4, 300 steps: J 1.2e-8, gradient 1.5e-7.
 
 The tests assert these figures with a margin of about 1.5x, so the stated
-accuracy is the one the tests check, including the full 2000-step horizon where
-the gradient error exceeds 1e-5.
+accuracy is the one the tests check, up to the full 2000-step horizon.
 """
 import numpy as np
 import pytest
@@ -44,7 +43,7 @@ def _rel(a, b):
     return float((a - b).abs().max() / b.abs().max())
 
 
-@pytest.mark.parametrize("steps,bounds", [(500, (5e-7, 2.5e-8, 4.5e-6)), (2000, (7e-6, 6e-8, 1.8e-5))])
+@pytest.mark.parametrize("steps,bounds", [(500, (5e-7, 2.5e-8, 2e-7)), (2000, (7e-6, 6e-8, 7e-7))])
 def test_fp32_bulk_error_at_the_2d_workload_horizon(steps, bounds):
     b_u, b_J, b_g = bounds
     s64 = Sem(2, 64, 7, 1e-3, precision="fp64")
@@ -71,4 +70,4 @@ def test_fp32_bulk_error_at_nu_1e_2_against_the_oracle():
     grad = grad.cpu().numpy()
     assert np.max(np.abs(uN - uNr)) <= 4e-7 * np.max(np.abs(uNr))
     assert abs(J - Jr) <= 8e-8 * abs(Jr)
-    assert np.max(np.abs(grad - lam)) <= 5e-7 * np.max(np.abs(lam))
+    assert np.max(np.abs(grad - lam)) <= 1e-7 * np.max(np.abs(lam))
