@@ -288,6 +288,26 @@ def test_full_size_3d_operators_on_sampled_nodes(prec, rtol):
             assert abs(JT[(c,) + nd] - JTr[c, k]) <= rtol * scaleT
 
 
+def test_fp32_rows_of_more_than_32_elements_on_sampled_nodes():
+    """E = 36 hexes per side, N = 7 (3 x 252^3 unknowns): the row-wise FP32 assembly covers each
+    grid row in two warp chunks (32 elements, then a ragged 4), with the periodic seam between the
+    last chunk and the first.  F and J^T on sampled nodes against the oracle."""
+    s, g = pair(3, 36, 7, nu=5e-4, precision="fp32_bulk")
+    x = g.coords()
+    u, v = inputs.field_3d(x, 1), inputs.field_3d(x, 2)
+    F, JT = s.rhs(u).cpu().numpy(), s.jacT(u, v).cpu().numpy()
+    N, G = g.N, g.G
+    nodes = _sample_nodes(g, np.random.default_rng(5), 24)
+    # nodes in the second chunk of a row (elements 32..35 along x) and at the seam
+    nodes += [(3, 5, 32 * N), (N, 0, 33 * N + 2), (0, 2 * N, G - 1), (7, 9, 31 * N + 6), (4, 4, 0)]
+    Fr, JTr = g.rhs_at(u, nodes), g.jacT_at(u, v, nodes)
+    sF, sT = np.max(np.abs(Fr)), np.max(np.abs(JTr))
+    for k, nd in enumerate(nodes):
+        for c in range(3):
+            assert abs(F[(c,) + nd] - Fr[c, k]) <= RTOL32 * sF
+            assert abs(JT[(c,) + nd] - JTr[c, k]) <= RTOL32 * sT
+
+
 @pytest.mark.parametrize("mode,slots", [("stages", 0), ("binomial", 3)])
 def test_graph_replay_equals_stream_launches(mode, slots):
     s, g = pair(2, 6, 7, nu=1e-3, ckpt=mode, ckpt_slots=slots)
