@@ -1,4 +1,4 @@
-"""The bench's multi-core driver of the oracle (cpu_baseline and --impl reference legs), on the CPU.
+"""The bench's multi-core evaluation of the oracle (cpu_baseline and --impl reference legs), on the CPU.
 
 It splits the oracle's element loop over a process pool; its F(u) and J(u)^T v must equal the
 oracle's own Grid.rhs and Grid.jacT up to the grouping of the gather-scatter sums."""
