@@ -39,7 +39,7 @@ size_t elem_smem_bytes(int op) {
     using Tl = Tile<NP>;
     const size_t tile = D == 3 ? Tl::S3 : (D == 2 ? Tl::S2 : 0);
     if (comp_parallel<T, D>()) return (size_t)(tiles_per_elem<D>(op) + 1) * tile * sizeof(T);
-    if (D == 3 && lean3<T, NP>()) return (size_t)lean_tiles_per_elem<D>(op) * tile * sizeof(T);
+    if (D == 3 && lean3_op<T, NP>(op)) return (size_t)lean_tiles_per_elem<D>(op) * tile * sizeof(T);
     return (size_t)tiles_per_elem<D>(op) * tile * sizeof(T);
 }
 
@@ -57,7 +57,7 @@ cudaError_t launch_elem_np(int op, const double* mats, const ElemArgs& a, cudaSt
         return launch_pdl(op1_kernel<T, NP>, dim3(blocks), dim3(threads), 0, s, M, a, op);
     } else {
         constexpr int TPE = D == 3 ? NP * NP : (comp_parallel<T, D>() ? 2 * NP : NP);
-        constexpr bool lean = D == 3 && lean3<T, NP>();
+        const bool lean = D == 3 && lean3_op<T, NP>(op);
         const size_t per = elem_smem_bytes<T, D, NP>(op);
         const int epb_max = lean ? 1 : std::max(1, std::min(256 / TPE, (int)(SMEM_TARGET / per)));
         // Balance the grid over the SMs: the fewest waves k of NUM_SMS blocks that
@@ -97,9 +97,12 @@ cudaError_t launch_elem_np(int op, const double* mats, const ElemArgs& a, cudaSt
             return launch_pdl(op2c_kernel<T, NP>, dim3(blocks), dim3(threads), smem, s, M, a, op);
         }
         void (*k)(const OpMats<T, NP>, const ElemArgs);
-        if constexpr (lean)
+        if constexpr (D == 3 && lean3<T, NP>())
             k = op == OP_RHS ? rhs3_lean_kernel<T, NP>
                              : (op == OP_JAC ? jac3_lean_kernel<T, NP> : jact3_lean_kernel<T, NP>);
+        else if constexpr (D == 3 && lean3_any<T, NP>())
+            k = lean ? jact3_lean_kernel<T, NP>   // lean3_op: J^T only
+                     : (op == OP_RHS ? rhs3_kernel<T, NP> : jac3_kernel<T, NP>);
         else if constexpr (D == 3 && std::is_same<T, double>::value && NP == 8)
             k = op == OP_RHS ? rhs3_f64_kernel<NP> : (op == OP_JAC ? jac3_f64_kernel<NP> : jact3_f64_kernel<NP>);
         else if constexpr (D == 3)
