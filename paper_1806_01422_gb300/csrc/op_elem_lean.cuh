@@ -25,20 +25,21 @@ __host__ __device__ constexpr bool lean3() {
     return NP >= 13;
 }
 
-// Lean kernels for one operator: always from n = 13, and for the double-float J^T from
-// n = 10.  Its eight 8-byte tiles per element take 70 KB at n = 10 and 120 KB at n = 12,
-// which leaves one 144-thread block per SM at n = 12 (4.5 warps); the six lean tiles let
-// two blocks share it.  (The lean double-float J needs 255 registers at n = 12, so J keeps
-// the plain kernel.)
+// Lean kernels for one operator: always from n = 13, and for the double-float J^T at
+// n = 12.  Its eight 8-byte tiles per element take 120 KB there, which leaves one
+// 144-thread block per SM (4.5 warps); the six lean tiles let two blocks share it, and
+// J^T went from 8.0 to 9.6 GDOF/s at order 11.  At n = 10 the lean kernel measured slower
+// (12.1 against 10.1 GDOF/s at order 9): three plain blocks already fit there.  (The lean
+// double-float J needs 255 registers at n = 12, so J keeps the plain kernel.)
 template <typename T, int NP>
 __host__ __device__ constexpr bool lean3_op(int op) {
-    return lean3<T, NP>() || (std::is_same<T, dfloat>::value && NP >= 10 && op == OP_JACT);
+    return lean3<T, NP>() || (std::is_same<T, dfloat>::value && NP == 12 && op == OP_JACT);
 }
 
 // Whether any operator of (T, NP) uses the lean kernels (they are compiled only then).
 template <typename T, int NP>
 __host__ __device__ constexpr bool lean3_any() {
-    return lean3<T, NP>() || (std::is_same<T, dfloat>::value && NP >= 10);
+    return lean3<T, NP>() || (std::is_same<T, dfloat>::value && NP == 12);
 }
 
 template <int D>
