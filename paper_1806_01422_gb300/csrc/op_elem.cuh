@@ -127,6 +127,12 @@ __device__ __forceinline__ T load3(T* tile, const void* g, int c, int ex, int ey
     const int nbij = (int)(i == 0 || i == N) + (int)(j == 0 || j == N);
     float ref_hi = 0.f, ref_lo = 0.f;
     if (RefSub<T>::on && !scale_mult && valid) read_pair(a, g, gidx3(c, ez * N, ey * N, ex * N, G), ref_hi, ref_lo);
+    // Index of node k of the column: its nodes are G^2 apart, and only node N of the last
+    // element along z wraps to gz = 0.  32-bit arithmetic suffices (fewer than 2^31 unknowns).
+    const unsigned G2 = (unsigned)G * (unsigned)G;
+    const unsigned col = (((unsigned)c * G + (unsigned)(ez * N)) * G + gy) * G + gx;
+    const unsigned zwrap = ez == a.E - 1 ? (unsigned)G * G2 : 0u;
+    auto node = [&](int k) -> unsigned { return col + (unsigned)k * G2 - (k == NP - 1 ? zwrap : 0u); };
     if constexpr (RefSub<T>::on) {
         // FP32 form: issue every load of the column before the first conversion, so that
         // the gather's latency is paid once per column rather than once per node
@@ -135,7 +141,7 @@ __device__ __forceinline__ T load3(T* tile, const void* g, int c, int ex, int ey
         for (int k = 0; k < NP; ++k) {
             hv[k] = 0.f;
             lv[k] = 0.f;
-            const size_t idx = gidx3(c, wrap(ez * N + k, G), gy, gx, G);
+            const unsigned idx = node(k);
             if (valid) {
                 if (a.in_f2) {
                     hv[k] = __ldg((const float*)g + idx);
@@ -156,8 +162,7 @@ __device__ __forceinline__ T load3(T* tile, const void* g, int c, int ex, int ey
         // double inputs: every load of the column first, then the conversions
         double xv[NP];
 #pragma unroll
-        for (int k = 0; k < NP; ++k)
-            xv[k] = valid ? __ldg((const double*)g + gidx3(c, wrap(ez * N + k, G), gy, gx, G)) : 0.0;
+        for (int k = 0; k < NP; ++k) xv[k] = valid ? __ldg((const double*)g + node(k)) : 0.0;
 #pragma unroll
         for (int k = 0; k < NP; ++k)
             tile[(k * NP + j) * Tl::P + i] = tile_of_double<T>(xv[k], scale_mult, nbij + (int)(k == 0 || k == N));
