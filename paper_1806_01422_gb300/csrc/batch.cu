@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(128) batch_asm2_kernel(const double* __restric
         for (int o = 0; o < NOUT; ++o) {
             const double ak[1] = {pick4(ep.alpha_k[o], nsh)};
             double v[1];
-            epi_output<1, NSRC>(ep.key[o], v, ak, s1, ep.beta[o], sv);
+            const int n1[1] = {nsh};
+            epi_output<1, NSRC>(ep.key[o], v, ak, s1, ep.beta[o], sv, n1);
             ov[o] = v[0];
             bad |= nonfinite_bits(v[0]);
         }

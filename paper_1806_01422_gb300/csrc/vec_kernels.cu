@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(128) assemble_kernel(const T* __restrict__ lve
         double ak[R], v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) ak[r] = pick4(ep.alpha_k[o], nsh[r]);
-        epi_output<R, NSRC>(ep.key[o], v, ak, sum, ep.beta[o], sv);
+        epi_output<R, NSRC>(ep.key[o], v, ak, sum, ep.beta[o], sv, nsh);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             ov[r][o] = v[r];
