@@ -23,7 +23,7 @@ void fill_opmats(void* dst, const double* mats) {
     OpMats<double, NP> M;
     split_eo<double, NP>(M.Dg, mats + 0 * NP * NP);
     split_eo<double, NP>(M.Sv, mats + 1 * NP * NP);
-    split_eo<double, NP>(M.Gv, mats + 2 * NP * NP);
+    split_eo<double, NP>(M.Gv, mats + 2 * NP * NP, 2.0);
     split_eo<double, NP>(M.Dd, mats + 3 * NP * NP);
     memcpy(dst, &M, sizeof(M));
 }

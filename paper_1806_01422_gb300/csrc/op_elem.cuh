@@ -273,12 +273,11 @@ __device__ __forceinline__ void jac_pass(const OpMats<T, NP>& M, const T* sUc, c
 template <typename T, int NP, int STRIDE, int D>
 __device__ __forceinline__ void jact_pass(const OpMats<T, NP>& M, T* const* sU, T* const* sZ, const T* rU,
                                           int l, int d, int base, T (&r)[NP]) {
-    T z[NP], q[NP];
+    T z[NP], u[NP];
     ld_line<T, NP, STRIDE>(sZ[l], base, z);
-    eo_apply<false, T, NP>(M.Gv, z, q);
 #pragma unroll
-    for (int m = 0; m < NP; ++m) q[m] = fma(with_ref(rU[d], sU[d][base + m * STRIDE]), z[m], q[m]);
-    eo_apply<false, T, NP>(M.Dd, q, r);
+    for (int m = 0; m < NP; ++m) u[m] = with_ref(rU[d], sU[d][base + m * STRIDE]);
+    gvdd_apply<T, NP>(M.Gv, M.Dd, z, u, r);
     if (l == d) {
 #pragma unroll
         for (int c = 0; c < D; ++c) {
@@ -745,13 +744,13 @@ __device__ __forceinline__ void jac2c_body(const OpMats<T, NP>& M, const ElemArg
 template <typename T, int NP, int D>
 __device__ __forceinline__ void jact_pass_rt(const OpMats<T, NP>& M, T* const* sU, T* const* sZ, const T* rU, int l,
                                              int d, int base, int stride, T (&r)[NP]) {
-    T z[NP], q[NP];
+    T z[NP], u[NP];
 #pragma unroll
-    for (int m = 0; m < NP; ++m) z[m] = sZ[l][base + m * stride];
-    eo_apply<false, T, NP>(M.Gv, z, q);
-#pragma unroll
-    for (int m = 0; m < NP; ++m) q[m] = fma(with_ref(rU[d], sU[d][base + m * stride]), z[m], q[m]);
-    eo_apply<false, T, NP>(M.Dd, q, r);
+    for (int m = 0; m < NP; ++m) {
+        z[m] = sZ[l][base + m * stride];
+        u[m] = with_ref(rU[d], sU[d][base + m * stride]);
+    }
+    gvdd_apply<T, NP>(M.Gv, M.Dd, z, u, r);
     if (l == d) {
 #pragma unroll 1
         for (int c = 0; c < D; ++c) {
@@ -851,12 +850,11 @@ __global__ void op1_kernel(const __grid_constant__ OpMats<T, NP> M, const ElemAr
 #pragma unroll
         for (int m = 0; m < NP; ++m) f[m] -= fma(with_ref(rw, w[m]), gu[m], with_ref(ru, u[m]) * gw[m]);
     } else {
-        T z[NP], q[NP], gu[NP];
+        T z[NP], uu[NP], gu[NP];
         load1<T, NP>(z, a.w, e, a, true);
-        eo_apply<false, T, NP>(M.Gv, z, q);
 #pragma unroll
-        for (int m = 0; m < NP; ++m) q[m] = fma(with_ref(ru, u[m]), z[m], q[m]);
-        eo_apply<false, T, NP>(M.Dd, q, f);
+        for (int m = 0; m < NP; ++m) uu[m] = with_ref(ru, u[m]);
+        gvdd_apply<T, NP>(M.Gv, M.Dd, z, uu, f);
         eo_apply<false, T, NP>(M.Dg, u, gu);
 #pragma unroll
         for (int m = 0; m < NP; ++m) f[m] = fma(-z[m], gu[m], f[m]);

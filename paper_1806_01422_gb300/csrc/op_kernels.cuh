@@ -67,7 +67,8 @@ template <typename T, int NP>
 struct OpMats {
     EOMat<T, NP> Dg;   // (2/h) Dhat                                antisymmetric: gradient
     EOMat<T, NP> Sv;   // -nu (2/h)^2 W^-1 Dhat^T W Dhat             symmetric: viscous term of F and J
-    EOMat<T, NP> Gv;   // nu (2/h) W Dhat W^-1                       antisymmetric: viscous flux of J^T
+    EOMat<T, NP> Gv;   // nu (2/h) W Dhat W^-1                       antisymmetric: viscous flux of J^T,
+                       //   stored with its even and odd halves doubled (gvdd_apply)
     EOMat<T, NP> Dd;   // -(2/h) Dhat^T                              antisymmetric: divergence (J^T)
 };
 
@@ -125,6 +126,41 @@ __device__ __forceinline__ void eo_apply(const EOMat<T, NP>& A, const T (&x)[NP]
     Pre<T, NP> p;
     pre_add<T, NP>(x, p);
     eo_apply<SYM, T, NP>(A, p, y);
+}
+
+// r = Dd (Gv z + u z) along one line (the J^T flux and its divergence), with G2
+// holding Gv's even and odd halves doubled (split_eo with scale 2; the middle row
+// of odd n as is).  With a = G2.e ze and b = G2.o zo, Gv z has
+// y_i = (a_i + b_i)/2 and y_{n-1-i} = (b_i - a_i)/2, so the pre-adds of
+// q = Gv z + u z that Dd takes are
+//   qe_i = b_i + u_i z_i + u_{n-1-i} z_{n-1-i},   qo_i = a_i + u_i z_i - u_{n-1-i} z_{n-1-i}
+// and, for odd n, qe_H = y_H + u_H z_H.  Gv's reconstruction, the advective
+// product and Dd's pre-adds fold into four multiply-adds per node pair, against
+// two adds, two multiply-adds and two adds the other way round.
+template <typename T, int NP>
+__device__ __forceinline__ void gvdd_apply(const EOMat<T, NP>& G2, const EOMat<T, NP>& Dd, const T (&z)[NP],
+                                           const T (&u)[NP], T (&r)[NP]) {
+    constexpr int H = NP / 2;
+    Pre<T, NP> pz, pq;
+    pre_add<T, NP>(z, pz);
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        T a = G2.e[i][0] * pz.xe[0];
+#pragma unroll
+        for (int j = 1; j < H + (NP & 1); ++j) a = fma(G2.e[i][j], pz.xe[j], a);
+        T b = G2.o[i][0] * pz.xo[0];
+#pragma unroll
+        for (int j = 1; j < H; ++j) b = fma(G2.o[i][j], pz.xo[j], b);
+        pq.xe[i] = fma(u[NP - 1 - i], z[NP - 1 - i], fma(u[i], z[i], b));
+        pq.xo[i] = fma(-u[NP - 1 - i], z[NP - 1 - i], fma(u[i], z[i], a));
+    }
+    if constexpr (NP & 1) {
+        T c = G2.m[0] * pz.xo[0];
+#pragma unroll
+        for (int j = 1; j < H; ++j) c = fma(G2.m[j], pz.xo[j], c);
+        pq.xe[H] = fma(u[H], z[H], c);
+    }
+    eo_apply<false, T, NP>(Dd, pq, r);
 }
 
 // ---------------------------------------------------------------- tile geometry

@@ -11,16 +11,18 @@
 namespace semk {
 
 // Even/odd halves of a centro-(anti)symmetric matrix (the storage is the same
-// for both symmetries; the kernels apply the matching reconstruction).
+// for both symmetries; the kernels apply the matching reconstruction), times
+// scale (a power of two, so the scaling is exact); the middle row of odd n is
+// never scaled.  J^T takes Gv with scale 2 (gvdd_apply).
 template <typename T, int NP>
-void split_eo(EOMat<T, NP>& M, const double* A) {
+void split_eo(EOMat<T, NP>& M, const double* A, double scale = 1.0) {
     constexpr int H = NP / 2;
     for (int i = 0; i < H; ++i) {
         for (int j = 0; j < H; ++j) {
-            M.e[i][j] = to_coeff<T>(0.5 * (A[i * NP + j] + A[i * NP + (NP - 1 - j)]));
-            M.o[i][j] = to_coeff<T>(0.5 * (A[i * NP + j] - A[i * NP + (NP - 1 - j)]));
+            M.e[i][j] = to_coeff<T>(0.5 * scale * (A[i * NP + j] + A[i * NP + (NP - 1 - j)]));
+            M.o[i][j] = to_coeff<T>(0.5 * scale * (A[i * NP + j] - A[i * NP + (NP - 1 - j)]));
         }
-        if (NP & 1) M.e[i][H] = to_coeff<T>(A[i * NP + H]);
+        if (NP & 1) M.e[i][H] = to_coeff<T>(scale * A[i * NP + H]);
     }
     for (int j = 0; j <= H; ++j) M.m[j] = to_coeff<T>((NP & 1) ? A[H * NP + j] : 0.0);
 }
@@ -48,7 +50,7 @@ cudaError_t launch_elem_np(int op, const double* mats, const ElemArgs& a, cudaSt
     OpMats<T, NP> M;
     split_eo<T, NP>(M.Dg, mats + 0 * NP * NP);
     split_eo<T, NP>(M.Sv, mats + 1 * NP * NP);
-    split_eo<T, NP>(M.Gv, mats + 2 * NP * NP);
+    split_eo<T, NP>(M.Gv, mats + 2 * NP * NP, 2.0);
     split_eo<T, NP>(M.Dd, mats + 3 * NP * NP);
     if (a.nelem <= 0) return cudaSuccess;
     if constexpr (D == 1) {
