@@ -671,26 +671,31 @@ def lbfgs_run(s, w, iters, dev):
             "J_history": [h[1] for h in hist]}
 
 
+def median_ms(fn, reps=30, warm=5):
+    """Median CUDA-event time (ms) of one call of fn over reps calls after warm calls, with an event
+    on the current stream between consecutive calls."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(warm):
+        fn()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for i in range(reps):
+        fn()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    return statistics.median(ev[i].elapsed_time(ev[i + 1]) for i in range(reps))
+
+
 def extras(s, u0, uo, w, dev):
     """Standalone operator throughput and the forward/adjoint split (outside the timed region)."""
     import torch
     stream = torch.cuda.current_stream(dev)
     out = s.empty()
 
-    def time_ms(fn, reps=30, warm=5):
-        for _ in range(warm):
-            fn()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        for _ in range(reps):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        return e0.elapsed_time(e1) / reps
-
-    tf = time_ms(lambda: s.rhs(u0, out))
-    tt = time_ms(lambda: s.jacT(u0, uo, out))
+    tf = median_ms(lambda: s.rhs(u0, out))
+    tt = median_ms(lambda: s.jacT(u0, uo, out))
     uN = s.empty()
     lam = s.empty()
     e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
@@ -707,8 +712,9 @@ def extras(s, u0, uo, w, dev):
             "forward_ms": fwd, "adjoint_ms": adj, "adjoint_forward_ratio": adj / fwd}
 
 
-def order_sweep(precisions=("fp64", "fp64_df", "fp32_bulk"), target=34e6, reps=10):
-    """Standalone F(u) and J^T v throughput over orders N at about `target` 3D unknowns."""
+def order_sweep(precisions=("fp64", "fp64_df", "fp32_bulk"), target=34e6, reps=20):
+    """Standalone F(u) and J^T v throughput over orders N at about `target` 3D unknowns (median of
+    reps applies)."""
     import torch
     from paper_1806_01422_gb300 import Sem, inputs
     rows = []
@@ -722,16 +728,7 @@ def order_sweep(precisions=("fp64", "fp64_df", "fp32_bulk"), target=34e6, reps=1
             out = s.empty()
             res = {}
             for name, fn in (("F", lambda: s.rhs(u, out)), ("JT", lambda: s.jacT(u, v, out))):
-                for _ in range(3):
-                    fn()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                torch.cuda.synchronize()
-                e0.record()
-                for _ in range(reps):
-                    fn()
-                e1.record()
-                torch.cuda.synchronize()
-                ms = e0.elapsed_time(e1) / reps
+                ms = median_ms(fn, reps=reps, warm=3)
                 res[name] = {"ms": ms, "gdofs": s.ndof / ms / 1e6}
             rows.append({"precision": prec, "N": N, "E": E, "unknowns": s.ndof, **res,
                          "JT_over_F": res["JT"]["ms"] / res["F"]["ms"]})
@@ -754,16 +751,7 @@ def contraction_ab(reps=20):
         ref = None
         for mode in ("cuda_core", "tensor"):
             s.set_contraction(mode)
-            for _ in range(3):
-                s.rhs(u, out)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            e0.record()
-            for _ in range(reps):
-                s.rhs(u, out)
-            e1.record()
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / reps
+            ms = median_ms(lambda: s.rhs(u, out), reps=reps, warm=3)
             s.profile(1)
             for _ in range(reps):
                 s.rhs(u, out)
