@@ -23,6 +23,34 @@ __host__ __device__ constexpr int tiles_per_elem(int op) {
     return (op == OP_RHS ? D : 2 * D) + (D == 3 ? 2 : 1);
 }
 
+// 3D kernels that run their passes from one copy of the code (df3_body): the
+// double-float ones (long unrolled passes) and FP32 with n >= 12 (register-bound
+// with three unrolled copies).
+template <typename T, int NP>
+__host__ __device__ constexpr bool shared_pass3() {
+    return std::is_same<T, dfloat>::value || (sizeof(T) == 4 && NP >= 12);
+}
+
+// FP32 F and J^T in 3D (the unrolled bodies): the y pass adds the x pass's partial
+// tile in place, so one partial tile serves both, at one more barrier per
+// component.  The results are the same bits (x part + y part, then the z part).  At
+// n = 8, F's four tiles instead of five let five blocks of four elements share an
+// SM instead of four; at every n the smaller shared-memory footprint leaves more of
+// the SM's on-chip memory to L1, which caches the neighbouring elements' shared
+// nodes of the tile gathers.  Measured per element pass: F at n = 6, 8, 10 gained
+// 11 %, 6 % and 1 %, and lost 6 % at n = 4 (the barrier); J^T gained 9 % at n = 7
+// and 8 % at n = 8, and lost 2 % at n = 9.  J keeps two partial tiles.
+template <typename T, int NP>
+__host__ __device__ constexpr bool one_partial3(int op) {
+    return sizeof(T) == 4 && !shared_pass3<T, NP>() && NP >= 6 && (op == OP_RHS || (op == OP_JACT && NP <= 8));
+}
+
+// Shared-memory tiles per element of the (non-lean) 3D element kernels.
+template <typename T, int NP>
+__host__ __device__ constexpr int tiles3(int op) {
+    return tiles_per_elem<3>(op) - (one_partial3<T, NP>(op) ? 1 : 0);
+}
+
 // ------------------------------------------------------------------ loaders
 // FP64 form: tiles hold the input doubles.
 // FP32 form: every input node is read as a float pair (hi, lo) -- either from the
@@ -89,6 +117,7 @@ __device__ __forceinline__ T tile_value(const ElemArgs& a, const void* g, size_t
         const double x = __ldg((const double*)g + i);
         return scale_mult ? scale_pow2_down(x, nb) : x;
     } else {
+        if (scale_mult && a.in_f2) return __ldg((const float*)g + i) * inv_mult<float>(nb);   // hi plane only
         float hi, lo;
         read_pair(a, g, i, hi, lo);
         if (scale_mult) return hi * inv_mult<float>(nb);
@@ -290,13 +319,6 @@ __device__ __forceinline__ void jact_pass(const OpMats<T, NP>& M, T* const* sU, 
     }
 }
 
-// 3D kernels that run their passes from one copy of the code (df3_body): the
-// double-float ones (long unrolled passes) and FP32 with n >= 12 (register-bound
-// with three unrolled copies).
-template <typename T, int NP>
-__host__ __device__ constexpr bool shared_pass3() {
-    return std::is_same<T, dfloat>::value || (sizeof(T) == 4 && NP >= 12);
-}
 
 template <typename T, int NP, int D>
 __device__ __forceinline__ void jact_pass_rt(const OpMats<T, NP>& M, T* const* sU, T* const* sZ, const T* rU, int l,
@@ -388,10 +410,11 @@ __device__ __forceinline__ void rhs3_body(const OpMats<T, NP>& M, const ElemArgs
     const int el = threadIdx.x / TPE, t = threadIdx.x % TPE;
     const int e = blockIdx.x * (blockDim.x / TPE) + el;
     const bool valid = e < a.nelem;
-    T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)el * tiles_per_elem<3>(OP_RHS) * S3;
+    constexpr bool ONE = one_partial3<T, NP>(OP_RHS);
+    T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)el * tiles3<T, NP>(OP_RHS) * S3;
     T* sU[3] = {sm, sm + S3, sm + 2 * S3};
     T* sF = sm + 3 * S3;
-    T* sA = sm + 4 * S3;
+    T* sA = ONE ? sF : sm + 4 * S3;
     const int ex = e % a.E, ey = (e / a.E) % a.E, ez = e / (a.E * a.E);
     T rU[3];
     load3_fields<T, NP>(sU, nullptr, a, ex, ey, ez, t, valid, rU, nullptr, false);
@@ -408,13 +431,27 @@ __device__ __forceinline__ void rhs3_body(const OpMats<T, NP>& M, const ElemArgs
         T r[NP];
         rhs_pass<T, NP, 1>(M, sU[c], sU[0], rU[0], xb, r);
         st_line<T, NP, 1>(sF, xb, r);
-        rhs_pass<T, NP, P>(M, sU[c], sU[1], rU[1], yb, r);
-        st_line<T, NP, P>(sA, yb, r);
-        __syncthreads();
-        rhs_pass<T, NP, S2>(M, sU[c], sU[2], rU[2], zb, r);
-        if (valid) {
+        if constexpr (ONE) {
+            // partial tile F = x part + y part (the sum the z pass would form: same bits)
+            __syncthreads();
+            rhs_pass<T, NP, P>(M, sU[c], sU[1], rU[1], yb, r);
 #pragma unroll
-            for (int m = 0; m < NP; ++m) out[(size_t)c * NP * NP * NP + m * NP * NP] = to_out(r[m] + (sF[zb + m * S2] + sA[zb + m * S2]));
+            for (int m = 0; m < NP; ++m) sF[yb + m * P] = sF[yb + m * P] + r[m];
+            __syncthreads();
+            rhs_pass<T, NP, S2>(M, sU[c], sU[2], rU[2], zb, r);
+            if (valid) {
+#pragma unroll
+                for (int m = 0; m < NP; ++m) out[(size_t)c * NP * NP * NP + m * NP * NP] = to_out(r[m] + sF[zb + m * S2]);
+            }
+        } else {
+            rhs_pass<T, NP, P>(M, sU[c], sU[1], rU[1], yb, r);
+            st_line<T, NP, P>(sA, yb, r);
+            __syncthreads();
+            rhs_pass<T, NP, S2>(M, sU[c], sU[2], rU[2], zb, r);
+            if (valid) {
+#pragma unroll
+                for (int m = 0; m < NP; ++m) out[(size_t)c * NP * NP * NP + m * NP * NP] = to_out(r[m] + (sF[zb + m * S2] + sA[zb + m * S2]));
+            }
         }
         __syncthreads();
     }
@@ -471,11 +508,12 @@ __device__ __forceinline__ void jact3_body(const OpMats<T, NP>& M, const ElemArg
     const int el = threadIdx.x / TPE, t = threadIdx.x % TPE;
     const int e = blockIdx.x * (blockDim.x / TPE) + el;
     const bool valid = e < a.nelem;
-    T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)el * tiles_per_elem<3>(OP_JACT) * S3;
+    constexpr bool ONE = one_partial3<T, NP>(OP_JACT);
+    T* sm = reinterpret_cast<T*>(smem_raw) + (size_t)el * tiles3<T, NP>(OP_JACT) * S3;
     T* sU[3] = {sm, sm + S3, sm + 2 * S3};
     T* sZ[3] = {sm + 3 * S3, sm + 4 * S3, sm + 5 * S3};
     T* sF = sm + 6 * S3;
-    T* sA = sm + 7 * S3;
+    T* sA = ONE ? sF : sm + 7 * S3;
     const int ex = e % a.E, ey = (e / a.E) % a.E, ez = e / (a.E * a.E);
     T rU[3], rZ[3];
     load3_fields<T, NP>(sU, sZ, a, ex, ey, ez, t, valid, rU, rZ, true);
@@ -492,13 +530,26 @@ __device__ __forceinline__ void jact3_body(const OpMats<T, NP>& M, const ElemArg
         T r[NP];
         jact_pass<T, NP, 1, 3>(M, sU, sZ, rU, l, 0, xb, r);
         st_line<T, NP, 1>(sF, xb, r);
-        jact_pass<T, NP, P, 3>(M, sU, sZ, rU, l, 1, yb, r);
-        st_line<T, NP, P>(sA, yb, r);
-        __syncthreads();
-        jact_pass<T, NP, S2, 3>(M, sU, sZ, rU, l, 2, zb, r);
-        if (valid) {
+        if constexpr (ONE) {
+            __syncthreads();
+            jact_pass<T, NP, P, 3>(M, sU, sZ, rU, l, 1, yb, r);
 #pragma unroll
-            for (int m = 0; m < NP; ++m) out[(size_t)l * NP * NP * NP + m * NP * NP] = to_out(r[m] + (sF[zb + m * S2] + sA[zb + m * S2]));
+            for (int m = 0; m < NP; ++m) sF[yb + m * P] = sF[yb + m * P] + r[m];
+            __syncthreads();
+            jact_pass<T, NP, S2, 3>(M, sU, sZ, rU, l, 2, zb, r);
+            if (valid) {
+#pragma unroll
+                for (int m = 0; m < NP; ++m) out[(size_t)l * NP * NP * NP + m * NP * NP] = to_out(r[m] + sF[zb + m * S2]);
+            }
+        } else {
+            jact_pass<T, NP, P, 3>(M, sU, sZ, rU, l, 1, yb, r);
+            st_line<T, NP, P>(sA, yb, r);
+            __syncthreads();
+            jact_pass<T, NP, S2, 3>(M, sU, sZ, rU, l, 2, zb, r);
+            if (valid) {
+#pragma unroll
+                for (int m = 0; m < NP; ++m) out[(size_t)l * NP * NP * NP + m * NP * NP] = to_out(r[m] + (sF[zb + m * S2] + sA[zb + m * S2]));
+            }
         }
         __syncthreads();
     }

@@ -42,6 +42,7 @@ size_t elem_smem_bytes(int op) {
     const size_t tile = D == 3 ? Tl::S3 : (D == 2 ? Tl::S2 : 0);
     if (comp_parallel<T, D>()) return (size_t)(tiles_per_elem<D>(op) + 1) * tile * sizeof(T);
     if (D == 3 && lean3_op<T, NP>(op)) return (size_t)lean_tiles_per_elem<D>(op) * tile * sizeof(T);
+    if constexpr (D == 3) return (size_t)tiles3<T, NP>(op) * tile * sizeof(T);
     return (size_t)tiles_per_elem<D>(op) * tile * sizeof(T);
 }
 

@@ -1648,11 +1648,12 @@ int sem_coords(sem_t h, double* x) {
 
 // FP32 form, standalone apply: the caller's doubles become float pairs once
 // (integer split, one pass over the unknowns) so that the element kernel reads
-// pair planes; the result is widened back to doubles by the assembly.
+// pair planes; the result is widened back to doubles by the assembly.  J^T reads
+// only the hi plane of v (Z = v / k in FP32), so only that plane is written.
 static int standalone(sem_t h, int op, const double* u, const double* w, double* out, cudaStream_t s) {
     if (!f32(h)) return apply(h, op, u, w, epi_plain(out, nullptr), s);
     cudaError_t e = launch_f64_to_f2(u, fl(vec(h, V_CUR0)), h->ndof, s);
-    if (e == cudaSuccess && w) e = launch_f64_to_f2(w, fl(vec(h, V_CUR1)), h->ndof, s);
+    if (e == cudaSuccess && w) e = launch_f64_to_f2(w, fl(vec(h, V_CUR1)), h->ndof, s, op == OP_JACT);
     if (e != cudaSuccess) return fail(SEM_ERR_CUDA, "conversion launch: %s", cudaGetErrorString(e));
     return apply(h, op, vec(h, V_CUR0), w ? vec(h, V_CUR1) : nullptr, epi_plain(out, nullptr), s, true);
 }

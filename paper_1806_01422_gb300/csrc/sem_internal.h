@@ -125,7 +125,9 @@ template <int NP>
 void fill_opmats(void* dst, const double* mats);   // even/odd split of the 4 element matrices (host)
 
 // FP32-form conversions at the API boundary (integer instructions for the split).
-cudaError_t launch_f64_to_f2(const double* in, float* out, size_t n, cudaStream_t s);
+// hi_only writes the hi plane alone, for an input the element kernels read as hi only
+// (Z = v / k of J^T).
+cudaError_t launch_f64_to_f2(const double* in, float* out, size_t n, cudaStream_t s, bool hi_only = false);
 cudaError_t launch_f2_to_f64(const float* in, double* out, size_t n, cudaStream_t s);
 // misfit with a float-pair state u and float-pair output lam (FP64 arithmetic)
 cudaError_t launch_objective_f2(const float* u, const double* uo, float* lam, double* partials, int nblocks,

@@ -628,13 +628,15 @@ cudaError_t launch_scale(double* out, const double* in, double alpha, size_t n, 
 }
 
 // ------------------------------------------------------------------ FP32 form
+// HI_ONLY: write the hi plane alone (an input the element kernels read as hi only, Z = v / k)
+template <bool HI_ONLY>
 __global__ void f64_to_f2_kernel(const double* __restrict__ in, float* __restrict__ out, size_t n) {
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += stride) {
         float hi, lo;
         split_bits(in[i], hi, lo);
         out[i] = hi;
-        out[n + i] = lo;
+        if (!HI_ONLY) out[n + i] = lo;
     }
 }
 
@@ -694,9 +696,12 @@ static unsigned grid_for(size_t n) {
     return (unsigned)(blocks ? blocks : 1);
 }
 
-cudaError_t launch_f64_to_f2(const double* in, float* out, size_t n, cudaStream_t s) {
+cudaError_t launch_f64_to_f2(const double* in, float* out, size_t n, cudaStream_t s, bool hi_only) {
     if (!n) return cudaSuccess;
-    f64_to_f2_kernel<<<grid_for(n), 256, 0, s>>>(in, out, n);
+    if (hi_only)
+        f64_to_f2_kernel<true><<<grid_for(n), 256, 0, s>>>(in, out, n);
+    else
+        f64_to_f2_kernel<false><<<grid_for(n), 256, 0, s>>>(in, out, n);
     return cudaGetLastError();
 }
 
