@@ -18,6 +18,7 @@ path has no exchange step between GPUs, so scaling is weak.  Prints one JSON lin
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -87,7 +88,7 @@ PEAK_DF_TFLOPS = 152 * 128 * 2.07e9 / 13 * 2 / 1e12
 # valid only while the kernel sources hash to the recorded value.
 TRAFFIC = {
     "rhs3_f64_kernel<8>@3d@fp64": {
-        "bytes": int(round((182861824 + 220680192) * 32 ** 3 / 28 ** 3)), "src": "89ab60694af9fbc1",
+        "bytes": int(round((181743360 + 220516352) * 32 ** 3 / 28 ** 3)), "src": "89ab60694af9fbc1",
         "capture": "dram__bytes_read.sum + dram__bytes_write.sum of one rhs3_f64_kernel<8> launch at 28^3 hexes, "
                    "N=7 (ncu --set full), scaled to 32^3 hexes by the element count"},
     "jact2_kernel<double,8>@2d@fp64": {
@@ -671,21 +672,32 @@ def lbfgs_run(s, w, iters, dev):
             "J_history": [h[1] for h in hist]}
 
 
-def median_ms(fn, reps=30, warm=5):
-    """Median CUDA-event time (ms) of one call of fn over reps calls after warm calls, with an event
-    on the current stream between consecutive calls."""
+def median_ms(fn, reps=30, warm=5, min_batch_ms=1.0):
+    """Median over reps repetitions of the CUDA-event time (ms) of one call of fn, after warm calls.
+    Each repetition times a batch of calls long enough (min_batch_ms) that the events' resolution
+    (about 0.5 us) does not matter, and divides by the batch size; the events are recorded on the
+    current stream between consecutive batches."""
     import torch
     stream = torch.cuda.current_stream()
     for _ in range(warm):
         fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(3):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    inner = max(1, int(math.ceil(min_batch_ms / max(e0.elapsed_time(e1) / 3, 1e-3))))
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
     torch.cuda.synchronize()
     ev[0].record(stream)
     for i in range(reps):
-        fn()
+        for _ in range(inner):
+            fn()
         ev[i + 1].record(stream)
     torch.cuda.synchronize()
-    return statistics.median(ev[i].elapsed_time(ev[i + 1]) for i in range(reps))
+    return statistics.median(ev[i].elapsed_time(ev[i + 1]) / inner for i in range(reps))
 
 
 def extras(s, u0, uo, w, dev):
