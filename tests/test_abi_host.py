@@ -45,7 +45,7 @@ def _create(L, dim, E, N, nu=0.01):
 
 @pytest.mark.parametrize("dim,E,N,nu", [(0, 2, 3, 0.1), (4, 2, 3, 0.1), (2, 0, 3, 0.1), (2, 2, 0, 0.1),
                                         (2, 2, 16, 0.1), (2, 2, 3, -1.0), (2, 2, 3, float("nan")),
-                                        (3, 2, 16, 0.1), (3, 2000, 7, 0.1)])
+                                        (3, 2, 16, 0.1), (3, 2000, 7, 0.1), (3, 128, 7, 0.1)])
 def test_create_rejects_bad_arguments(L, dim, E, N, nu):
     rc, h = _create(L, dim, E, N, nu)
     assert rc == L.SEM_ERR_ARG and not h.value
@@ -56,6 +56,11 @@ def test_create_is_host_only_and_counts_unique_dof(L):
     rc, h = _create(L, 3, 32, 7)
     assert rc == L.SEM_OK
     assert L.lib().sem_ndof(h) == 3 * 224 ** 3
+    L.lib().sem_destroy(h)
+    # the largest 3D grid at N = 7 below 2^31 unknowns (E = 128 is refused above)
+    rc, h = _create(L, 3, 127, 7)
+    assert rc == L.SEM_OK
+    assert L.lib().sem_ndof(h) == 3 * 889 ** 3 < 2 ** 31
     L.lib().sem_destroy(h)
     o = L.sem_opts(dim=3, E=2, N=15, nu=0.1, precision=L.SEM_PREC_FP32_BULK)
     h = ctypes.c_void_p()
