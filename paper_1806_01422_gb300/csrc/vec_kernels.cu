@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(128) assemble_f32_kernel(const float* __restri
     }
 }
 
-// Row-wise FP32 assembly for d = 3 (n = 8 and n = 16).  The node kernel above
+// Row-wise FP32 assembly for d = 3 (used at n = 8).  The node kernel above
 // spends most of its issue slots on per-node index arithmetic; here one warp owns
 // a chunk of one grid row along x (component c, rows gy and gz, up to 32
 // elements along x) and the index work is done once per row.
@@ -392,8 +392,10 @@ cudaError_t launch_rows_f32(const float* lvec, const AsmArgs& a, const EpiF2& e2
                       a, e2, nchunk);
 }
 
-// The row kernel serves these point counts (n a multiple of 4 for the vector loads).
-__host__ __device__ constexpr bool rows_f32_np(int np) { return np == 8 || np == 16; }
+// The row kernel serves n = 8 (the vector loads need n a multiple of 4).  At n = 16 the
+// node-per-thread kernel measured faster (the N = 15 FP32 gradient at 16^3 hexes went from
+// 0.435 to 0.442 evaluations/s with it): with 16 elements per grid row, half of each warp's
+// lanes idle in the row gather.
 
 template <int NP>
 cudaError_t dispatch_rows_f32(const float* lvec, const AsmArgs& a, const EpiF2& e2, int nout, int nsrc, bool f2,
@@ -489,7 +491,6 @@ cudaError_t launch_assemble(bool lvec_fp32, const void* lvec, const AsmArgs& a_i
             if (a.D == 1) return launch_pdl(assemble_f32_kernel<1, 1, 0, false>, grid, dim3(threads), 0, s, (const float*)lvec, a, e2);
             if (a.D == 2) return launch_pdl(assemble_f32_kernel<2, 1, 0, false>, grid, dim3(threads), 0, s, (const float*)lvec, a, e2);
             if (a.NP == 8) return dispatch_rows_f32<8>((const float*)lvec, a, e2, 1, 0, false, s);
-            if (a.NP == 16) return dispatch_rows_f32<16>((const float*)lvec, a, e2, 1, 0, false, s);
             return launch_pdl(assemble_f32_kernel<3, 1, 0, false>, grid, dim3(threads), 0, s, (const float*)lvec, a, e2);
         }
         EpiF2 e2{};
@@ -516,7 +517,6 @@ cudaError_t launch_assemble(bool lvec_fp32, const void* lvec, const AsmArgs& a_i
         default: SEMK_F2_NS(D, 3) break;      \
     }
         if (a.D == 3 && a.NP == 8) return dispatch_rows_f32<8>((const float*)lvec, a, e2, ep.nout, ep.nsrc, true, s);
-        if (a.D == 3 && a.NP == 16) return dispatch_rows_f32<16>((const float*)lvec, a, e2, ep.nout, ep.nsrc, true, s);
         if (a.D == 1) { SEMK_F2_NO(1) }
         else if (a.D == 2) { SEMK_F2_NO(2) }
         else { SEMK_F2_NO(3) }
