@@ -72,6 +72,18 @@ def test_operators_match_oracle_fp32_bulk(dim, E, N):
     assert max(errs.values()) < RTOL32, errs
 
 
+# Every 3D FP32 element-pass layout: two partial tiles (n = 4, 5), one partial tile for F and
+# J^T (n = 6..8), one for F only (n = 9..11), the shared pass code (n = 12) and the lean kernels
+# (n = 13..16).
+@pytest.mark.parametrize("E,N", [(3, 3), (3, 4), (3, 5), (2, 6), (2, 8), (2, 9), (2, 10), (2, 11), (2, 12), (2, 14)])
+def test_fp32_bulk_3d_operators_at_every_pass_layout(E, N):
+    s, g = pair(3, E, N, nu=FP32_NU[3], precision="fp32_bulk")
+    u, w = smooth(g, 1), smooth(g, 2)
+    errs = {"F": relerr(s.rhs(u), g.rhs(u)), "J": relerr(s.jac(u, w), g.jac(u, w)),
+            "JT": relerr(s.jacT(u, w), g.jacT(u, w))}
+    assert max(errs.values()) < RTOL32, errs
+
+
 @pytest.mark.parametrize("dim,E,N,scheme,steps,dt", [(2, 8, 7, "ssprk3", 20, 2e-4), (3, 4, 7, "rk4", 8, 2.5e-4),
                                                     (1, 16, 7, "rk4", 50, 1e-3)])
 def test_fp32_bulk_gradient_matches_fp64_oracle(dim, E, N, scheme, steps, dt):
