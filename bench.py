@@ -460,6 +460,13 @@ def roofline_of(prof, args, w, s, precision):
         if dfk:
             roof["peak_note"] = ("double-float multiply-add rate of the FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz "
                                  "/ 13 FP32 operations per multiply-add, x 2 flop")
+        # the second roof: the operator's minimum HBM bytes per launch (16 B per unknown for F: u in, F out;
+        # 24 B for J and J^T: two inputs, one output) over the same launch time
+        ndof = sum(w["dim"] * (E * N) ** w["dim"] for E, N in shapes)
+        alg_bytes = (16 if dom == "rhs" else 24) * ndof
+        hbm = alg_bytes / avg_s / 1e9
+        roof["hbm"] = {"algorithmic_bytes": alg_bytes, "achieved": hbm, "peak": args.hbm_peak, "unit": "GB/s",
+                       "frac": hbm / args.hbm_peak}
     key = "%s@%s@%s" % (roof["kernel"], args.workload, precision)
     tr = TRAFFIC.get(key)
     tr_ok = tr and tr["src"] == kernel_src_hash("assemble" if dom == "assemble" else "elem")

@@ -33,6 +33,9 @@ def test_element_kernel_roofline_from_sampled_times():
     assert r["peak"] == pytest.approx(bench.PEAK_FP64_TFLOPS)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert r["avg_launch_us"] == pytest.approx(53.0)
+    # the HBM roof of the same launch: 24 B per unique unknown (u and v in, J^T v out)
+    assert r["hbm"]["algorithmic_bytes"] == 24 * 2 * 448 ** 2
+    assert r["hbm"]["frac"] == pytest.approx(24 * 2 * 448 ** 2 / 53e-6 / 1e9 / 6795.8)
     # the recorded DRAM traffic is reported only while the kernel sources hash to its capture
     tr = bench.TRAFFIC["jact2_kernel<double,8>@2d@fp64"]
     expect = tr["bytes"] if tr["src"] == bench.kernel_src_hash("elem") else None
